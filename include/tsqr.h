@@ -1,0 +1,206 @@
+/*
+ * tsqr.h -- C ABI of the GB300 TSQR / CAQR library (libtsqr_gb300.so).
+ *
+ * The library factors a tall-skinny m x n matrix A (m >= n) stored in a 1-D
+ * block-row layout (Section 2, the problem statement of TSQR) into
+ *     A = Q R,   R upper triangular with diag(R) >= 0,
+ * where Q is kept implicitly as a product of block-diagonal orthogonal
+ * factors, one per tree level, as in Eq. TSQR_binarytree_4 (Section 2.1):
+ * one Householder QR per leaf (row block), then structured QRs of stacked R
+ * triangles up a reduction tree.  CAQR
+ * (Section 3) factors a general m x n matrix panel by panel with TSQR and
+ * applies each panel's Q^T to the trailing matrix.
+ *
+ * Conventions shared by every entry point:
+ *   - All matrix pointers are DEVICE pointers; matrices are column-major,
+ *     element (i, j) at p[i + j * ld], with ld >= number of rows.
+ *   - Element type: the FP64 entry points take double; the _f32 entry points
+ *     take float storage and keep column norms, Householder vectors and tau
+ *     generation in FP64 (the mixed-precision form).  Entry points that take
+ *     a handle and a void* operate in the handle's element type.
+ *   - Every call is asynchronous on `stream` (NULL = the legacy default
+ *     stream) and returns after enqueuing its kernels.  The return value
+ *     reports argument, launch and allocation errors only.  Device-side
+ *     conditions (non-finite input, a bounded wait that gave up) are latched
+ *     in the handle's status word and returned by tsqr_sync_status().
+ *   - Return codes: 0 on success; -i if argument i (1-based) is invalid, in
+ *     the style of LAPACK's info; a positive TSQR_ERR_* code otherwise.
+ *   - Quick returns: m = 0 or n = 0 succeed and enqueue nothing.  m < n is
+ *     an argument error (the paper assumes m >= n, Section 2).
+ *   - Handles are opaque and library-owned; free them with tsqr_q_destroy
+ *     (or caqr_q_destroy).  A handle BORROWS the matrix A it factored: the
+ *     leaf Householder vectors live in A's storage, so the caller keeps A
+ *     alive and unmodified until the handle is destroyed.  A handle is used
+ *     by one stream at a time.
+ */
+#ifndef TSQR_GB300_H
+#define TSQR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tsqr_stream_t; /* same type as cudaStream_t */
+typedef struct tsqr_q_s* tsqr_q_t;         /* TSQR Q-tree handle */
+typedef struct caqr_q_s* caqr_q_t;         /* CAQR handle: one Q-tree per panel */
+
+enum tsqr_status_code {
+  TSQR_OK = 0,
+  TSQR_ERR_CUDA = 1,        /* a CUDA runtime call failed */
+  TSQR_ERR_NOMEM = 2,       /* device workspace allocation failed */
+  TSQR_ERR_TIMEOUT = 3,     /* a device-side bounded wait gave up */
+  TSQR_ERR_NONFINITE = 4,   /* NaN or Inf met in a column norm or pivot */
+  TSQR_ERR_UNSUPPORTED = 5, /* shape / precision combination not supported */
+  TSQR_ERR_HANDLE = 6       /* NULL, destroyed or mismatched handle */
+};
+
+enum tsqr_precision {
+  TSQR_PREC_FP64 = 0, /* FP64 storage and arithmetic */
+  TSQR_PREC_FP32 = 1  /* FP32 storage and products; FP64 norms, vectors, tau */
+};
+
+/* Tuning knobs; a zero field means "choose automatically". */
+typedef struct tsqr_opts_s {
+  int64_t leaf_rows; /* nominal leaf height h (>= n); rows per leaf block (Section 2.1) */
+  int32_t arity;     /* reduction-tree arity q >= 2 (Section 2.1: any tree is valid) */
+  int32_t flags;     /* reserved, must be 0 */
+} tsqr_opts_t;
+
+/* ---------------------------------------------------------------- TSQR -- */
+
+/*
+ * tsqr_factor: R and the Q-tree of A (Section 2.1, Eqs. TSQR_binarytree_1..4).
+ *   m, n   : rows and columns, m >= n >= 0.
+ *   A      : device, m x n, lda >= max(1, m).  Overwritten: each leaf's rows
+ *            hold its Householder vectors below the diagonal (unit diagonal
+ *            implicit) and the leaf R factor on and above it.
+ *   R      : device, n x n, ldr >= max(1, n).  Receives R with diag(R) >= 0;
+ *            entries below the diagonal are set to 0.
+ *   opts   : NULL or tuning knobs (leaf height, tree arity).
+ *   q      : receives a new handle; NULL to discard Q (R only).
+ * Leaves are consecutive row blocks of height h; the last leaf takes the
+ * remainder, merged into the previous leaf when it would have fewer than n
+ * rows.  Tree nodes factor q stacked upper triangles without touching their
+ * zeros (Section 2.1, structured local QR; Section 2.2, 2n^3/3 flops per
+ * binary node).  The signs d = sign(diag R_root) (sign(0) = +1) are applied
+ * to R and recorded in the handle, so apply/form calls use Q D.
+ */
+int tsqr_factor(int64_t m, int64_t n, double* A, int64_t lda, double* R, int64_t ldr,
+                const tsqr_opts_t* opts, tsqr_q_t* q, tsqr_stream_t stream);
+int tsqr_factor_f32(int64_t m, int64_t n, float* A, int64_t lda, float* R, int64_t ldr,
+                    const tsqr_opts_t* opts, tsqr_q_t* q, tsqr_stream_t stream);
+
+/*
+ * Plan-once form: tsqr_q_create allocates a handle and all of its device
+ * workspace for an m x n problem (precision TSQR_PREC_*); tsqr_refactor then
+ * factors a new matrix of that shape with no allocation, which makes the
+ * call safe inside CUDA stream capture.  tsqr_factor = create + refactor.
+ */
+int tsqr_q_create(int64_t m, int64_t n, int32_t precision, const tsqr_opts_t* opts, tsqr_q_t* q,
+                  tsqr_stream_t stream);
+int tsqr_refactor(tsqr_q_t q, void* A, int64_t lda, void* R, int64_t ldr, tsqr_stream_t stream);
+
+/*
+ * tsqr_apply_qt: C <- Q^T C for the square m x m Q of the handle, C m x k
+ * (device, ldc >= m).  Applied as the transpose of Eq. TSQR_binarytree_4:
+ * leaf factors first, then tree levels bottom-up, then D on rows 0..n-1.
+ * The top n rows of the result are the unique product with the thin Q; the
+ * remaining rows depend on the tree.  k = 0 is a quick return.
+ */
+int tsqr_apply_qt(tsqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream);
+
+/* tsqr_apply_q: C <- Q C (reverse order: D, tree top-down, leaves). */
+int tsqr_apply_q(tsqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream);
+
+/*
+ * tsqr_form_q: the thin Q (m x n, device, ldq >= m) = Q_tree [I_n; 0] D
+ * (Section 2.1: Q factors with n columns).  Q must not alias A.
+ */
+int tsqr_form_q(tsqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream);
+
+/*
+ * tsqr_sync_status: waits for the handle's work on `stream`, returns and
+ * clears the latched device status (TSQR_OK, TSQR_ERR_NONFINITE, ...).
+ */
+int tsqr_sync_status(tsqr_q_t q, tsqr_stream_t stream);
+
+/*
+ * tsqr_q_info: shape and plan of a handle.  Any output pointer may be NULL.
+ * levels counts tree levels above the leaves.
+ */
+int tsqr_q_info(tsqr_q_t q, int64_t* m, int64_t* n, int32_t* precision, int64_t* leaves,
+                int64_t* leaf_rows, int32_t* arity, int32_t* levels);
+
+/* tsqr_q_destroy: frees the handle and its workspace (after its queued work). */
+int tsqr_q_destroy(tsqr_q_t q);
+
+/* ---------------------------------------------------------------- CAQR -- */
+
+/*
+ * caqr_factor: right-looking Householder QR whose panel factorisation is
+ * TSQR (Section 3).
+ *   A (device, m x n, lda >= m, m >= n) is overwritten by R in its upper
+ *   triangle (diag(R) >= 0) and the panels' leaf Householder vectors below.
+ *   b is the panel width (1 <= b; the last panel may be narrower).
+ *   update_precision: TSQR_PREC_FP64 only for FP64 storage.
+ * For panel j the trailing columns receive (Q_j D_j)^T: first the leaf
+ * blocks, then the tree nodes on stacked b-row slices (Section 3.1), then
+ * the panel's signs, so rows of R stay consistent without a later fix.
+ */
+int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
+                const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream);
+
+/* caqr_apply_qt: C (m x k, ldc >= m) <- Q^T C, panels in factorisation order. */
+int caqr_apply_qt(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream);
+
+/* caqr_apply_q: C <- Q C, panels in reverse order. */
+int caqr_apply_q(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream);
+
+/* caqr_form_q: thin Q (m x n, ldq >= m), Q must not alias A. */
+int caqr_form_q(caqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream);
+
+int caqr_sync_status(caqr_q_t q, tsqr_stream_t stream);
+int caqr_q_destroy(caqr_q_t q);
+
+/* ----------------------------------------------------------- tracing -- */
+
+/*
+ * Per-stage device time of a handle's calls, measured with CUDA events that
+ * the library records on each call's stream around its kernel launches.
+ * Stages follow the cost terms of Section 2.2: the leaf QRs, the tree levels
+ * (including the sign fix), the leaf block-reflector applications (apply,
+ * form Q), and the tree-level applications.
+ */
+enum tsqr_stage {
+  TSQR_STAGE_LEAF_FACTOR = 0,
+  TSQR_STAGE_TREE_FACTOR = 1,
+  TSQR_STAGE_LEAF_APPLY = 2,
+  TSQR_STAGE_TREE_APPLY = 3,
+  TSQR_NUM_STAGES = 4
+};
+
+/* tsqr_q_set_timing: enable != 0 clears the totals and starts recording,
+ * enable == 0 stops recording (totals are kept). */
+int tsqr_q_set_timing(tsqr_q_t q, int32_t enable);
+
+/* tsqr_q_stage_times: waits for the recorded events and writes, for stages
+ * 0..count-1, the summed milliseconds (ms[i]) and the number of kernel
+ * launches (launches[i]) since timing was enabled.  Either array may be NULL. */
+int tsqr_q_stage_times(tsqr_q_t q, double* ms, int64_t* launches, int32_t count);
+
+/* -------------------------------------------------------------- misc -- */
+
+/* Static string for a return code. */
+const char* tsqr_status_string(int code);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int tsqr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSQR_GB300_H */

@@ -1,0 +1,251 @@
+"""GB300 TSQR / CAQR: Python binding of libtsqr_gb300.so (include/tsqr.h).
+
+The binding only marshals arguments: torch supplies device memory and the
+current CUDA stream, every step of the factorisation runs in the library's
+CUDA kernels.  Matrices are column-major torch tensors of shape (m, n) with
+stride (1, ld), ld >= m -- e.g. ``colmajor(m, n)`` or ``X.t().contiguous().t()``.
+
+    R, q = tsqr_factor(A)          # A is overwritten by the leaf reflectors
+    Q = q.form_q()                 # thin Q, A = Q R, diag(R) >= 0
+    q.apply_qt(C)                  # C <- Q^T C in place
+"""
+from __future__ import annotations
+
+import ctypes
+
+from ._lib import TsqrError, TsqrOpts, check, lib
+
+__all__ = [
+    "TsqrError", "QTree", "CaqrQ", "colmajor", "as_colmajor", "tsqr_factor", "tsqr_q_create",
+    "caqr_factor", "PREC_FP64", "PREC_FP32",
+]
+
+PREC_FP64 = 0
+PREC_FP32 = 1
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def colmajor(m: int, n: int, dtype=None, device="cuda"):
+    """Uninitialised m x n column-major tensor (shape (m, n), stride (1, m))."""
+    torch = _torch()
+    return torch.empty((n, m), dtype=dtype or torch.float64, device=device).t()
+
+
+def as_colmajor(t):
+    """Column-major copy of a 2-D tensor (no copy if already column-major)."""
+    if t.dim() == 2 and t.stride(0) == 1 and t.stride(1) >= t.shape[0]:
+        return t
+    return t.t().contiguous().t()
+
+
+def _ld(t, name: str) -> int:
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    m, n = t.shape
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if n <= 1:
+        if m > 1 and n == 1 and t.stride(0) != 1:
+            raise ValueError(f"{name} must be column-major (unit row stride)")
+        return max(1, m, t.stride(1) if n == 1 else m)
+    if t.stride(0) != 1 or t.stride(1) < m:
+        raise ValueError(f"{name} must be column-major (stride (1, ld) with ld >= {m}); use as_colmajor()")
+    return t.stride(1)
+
+
+def _prec(dtype) -> int:
+    torch = _torch()
+    if dtype == torch.float64:
+        return PREC_FP64
+    if dtype == torch.float32:
+        return PREC_FP32
+    raise TypeError(f"unsupported dtype {dtype}: float64 or float32")
+
+
+def _stream(t):
+    torch = _torch()
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _opts(leaf_rows: int, arity: int):
+    return TsqrOpts(int(leaf_rows), int(arity), 0)
+
+
+class QTree:
+    """Handle of a TSQR factorisation: Q as per-level orthogonal factors (Section 2.1).
+
+    Holds a reference to the factored matrix, whose storage keeps the leaf
+    Householder vectors.
+    """
+
+    def __init__(self, ptr, m: int, n: int, dtype, A=None):
+        self._ptr = ptr
+        self.m, self.n, self.dtype = m, n, dtype
+        self.A = A
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("handle already destroyed")
+        return self._ptr
+
+    def info(self) -> dict:
+        m, n, lv, h = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        p, q, lev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().tsqr_q_info(self.ptr, ctypes.byref(m), ctypes.byref(n), ctypes.byref(p), ctypes.byref(lv),
+                                ctypes.byref(h), ctypes.byref(q), ctypes.byref(lev)), "tsqr_q_info")
+        return {"m": m.value, "n": n.value, "precision": p.value, "leaves": lv.value, "leaf_rows": h.value,
+                "arity": q.value, "levels": lev.value}
+
+    def refactor(self, A, R=None):
+        """Factor a new matrix of the handle's shape; no allocation.  Returns R."""
+        if tuple(A.shape) != (self.m, self.n) or A.dtype != self.dtype:
+            raise ValueError("A does not match the handle's shape / dtype")
+        lda = _ld(A, "A")
+        if R is None:
+            R = colmajor(self.n, self.n, self.dtype, A.device)
+        ldr = _ld(R, "R")
+        check(lib().tsqr_refactor(self.ptr, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(R.data_ptr()), ldr,
+                                  _stream(A)), "tsqr_refactor")
+        self.A = A
+        return R
+
+    def _apply(self, fn, C, name):
+        if C.dtype != self.dtype or C.shape[0] != self.m:
+            raise ValueError(f"C must be {self.m} x k of dtype {self.dtype}")
+        ldc = _ld(C, "C")
+        check(fn(self.ptr, C.shape[1], ctypes.c_void_p(C.data_ptr()), ldc, _stream(C)), name)
+        return C
+
+    def apply_qt(self, C):
+        """C <- Q^T C in place (square Q); returns C."""
+        return self._apply(lib().tsqr_apply_qt, C, "tsqr_apply_qt")
+
+    def apply_q(self, C):
+        """C <- Q C in place (square Q); returns C."""
+        return self._apply(lib().tsqr_apply_q, C, "tsqr_apply_q")
+
+    def form_q(self, Q=None):
+        """Thin Q (m x n, column-major) including the sign vector."""
+        if Q is None:
+            Q = colmajor(self.m, self.n, self.dtype, self.A.device if self.A is not None else "cuda")
+        ldq = _ld(Q, "Q")
+        check(lib().tsqr_form_q(self.ptr, ctypes.c_void_p(Q.data_ptr()), ldq, _stream(Q)), "tsqr_form_q")
+        return Q
+
+    STAGES = ("leaf_factor", "tree_factor", "leaf_apply", "tree_apply")
+
+    def set_timing(self, enable: bool = True) -> None:
+        """Record CUDA events around each stage of later calls (clears totals when enabling)."""
+        check(lib().tsqr_q_set_timing(self.ptr, 1 if enable else 0), "tsqr_q_set_timing")
+
+    def stage_times(self) -> dict:
+        """{stage: (total ms, kernel launches)} since timing was enabled (waits for the events)."""
+        ms = (ctypes.c_double * 4)()
+        nl = (ctypes.c_int64 * 4)()
+        check(lib().tsqr_q_stage_times(self.ptr, ms, nl, 4), "tsqr_q_stage_times")
+        return {name: (ms[i], nl[i]) for i, name in enumerate(self.STAGES)}
+
+    def sync_status(self) -> int:
+        """Wait for queued work and return the device status code (0 = ok)."""
+        torch = _torch()
+        return lib().tsqr_sync_status(self.ptr, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def destroy(self):
+        if self._ptr:
+            lib().tsqr_q_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def tsqr_q_create(m: int, n: int, dtype=None, device="cuda", leaf_rows: int = 0, arity: int = 0) -> QTree:
+    """Plan and allocate a handle for m x n problems; factor with QTree.refactor."""
+    torch = _torch()
+    dtype = dtype or torch.float64
+    h = ctypes.c_void_p()
+    o = _opts(leaf_rows, arity)
+    check(lib().tsqr_q_create(m, n, _prec(dtype), ctypes.byref(o), ctypes.byref(h),
+                              ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)), "tsqr_q_create")
+    return QTree(h, m, n, dtype)
+
+
+def tsqr_factor(A, R=None, leaf_rows: int = 0, arity: int = 0, keep_q: bool = True):
+    """TSQR of the column-major m x n CUDA tensor A (overwritten).  Returns (R, QTree or None)."""
+    m, n = A.shape
+    lda = _ld(A, "A")
+    if R is None:
+        R = colmajor(n, n, A.dtype, A.device)
+    ldr = _ld(R, "R")
+    h = ctypes.c_void_p()
+    o = _opts(leaf_rows, arity)
+    fn = lib().tsqr_factor if _prec(A.dtype) == PREC_FP64 else lib().tsqr_factor_f32
+    check(fn(m, n, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(R.data_ptr()), ldr, ctypes.byref(o),
+             ctypes.byref(h) if keep_q else None, _stream(A)), "tsqr_factor")
+    return R, (QTree(h, m, n, A.dtype, A) if keep_q and h.value else None)
+
+
+class CaqrQ:
+    """Handle of a CAQR factorisation: one Q-tree per panel (Section 3)."""
+
+    def __init__(self, ptr, m: int, n: int, dtype, A):
+        self._ptr, self.m, self.n, self.dtype, self.A = ptr, m, n, dtype, A
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("handle already destroyed")
+        return self._ptr
+
+    def _apply(self, fn, C, name):
+        if C.dtype != self.dtype or C.shape[0] != self.m:
+            raise ValueError(f"C must be {self.m} x k of dtype {self.dtype}")
+        check(fn(self.ptr, C.shape[1], ctypes.c_void_p(C.data_ptr()), _ld(C, "C"), _stream(C)), name)
+        return C
+
+    def apply_qt(self, C):
+        return self._apply(lib().caqr_apply_qt, C, "caqr_apply_qt")
+
+    def apply_q(self, C):
+        return self._apply(lib().caqr_apply_q, C, "caqr_apply_q")
+
+    def form_q(self, Q=None):
+        if Q is None:
+            Q = colmajor(self.m, self.n, self.dtype, self.A.device)
+        check(lib().caqr_form_q(self.ptr, ctypes.c_void_p(Q.data_ptr()), _ld(Q, "Q"), _stream(Q)), "caqr_form_q")
+        return Q
+
+    def sync_status(self) -> int:
+        torch = _torch()
+        return lib().caqr_sync_status(self.ptr, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def destroy(self):
+        if self._ptr:
+            lib().caqr_q_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def caqr_factor(A, b: int = 64, update_precision: int = PREC_FP64, leaf_rows: int = 0, arity: int = 0,
+                keep_q: bool = True):
+    """CAQR of the column-major m x n CUDA tensor A in place: R lands in A's upper triangle."""
+    m, n = A.shape
+    h = ctypes.c_void_p()
+    o = _opts(leaf_rows, arity)
+    check(lib().caqr_factor(m, n, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), b, update_precision, ctypes.byref(o),
+                            ctypes.byref(h) if keep_q else None, _stream(A)), "caqr_factor")
+    return CaqrQ(h, m, n, A.dtype, A) if keep_q and h.value else None

@@ -1,0 +1,680 @@
+// C ABI of the TSQR / CAQR library: argument checks, the tree plan, device
+// workspace, and the launch sequences of Section 2.1 (TSQR) and Section 3
+// (CAQR).  All arithmetic runs in the kernels of leaf_factor.cu,
+// node_factor.cu and apply.cu.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "../../include/tsqr.h"
+#include "tsqr_internal.cuh"
+
+namespace tsqr {
+size_t node_factor_smem(int n, int q, size_t elem);
+size_t leaf_apply_smem(int n, size_t elem);
+size_t node_apply_smem(int n, size_t elem);
+}  // namespace tsqr
+
+using namespace tsqr;
+
+namespace {
+
+constexpr uint32_t kTsqrMagic = 0x54535152u;  // "TSQR"
+constexpr uint32_t kCaqrMagic = 0x43415152u;  // "CAQR"
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int max_smem_optin() {
+  static int cached = -1;
+  if (cached < 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      v = 227 * 1024;
+    cached = v;
+  }
+  return cached;
+}
+
+}  // namespace
+
+struct tsqr_q_s {
+  uint32_t magic = kTsqrMagic;
+  int32_t prec = TSQR_PREC_FP64;
+  size_t es = 8;
+  int64_t m = 0, n = 0;
+  int64_t h = 0, nleaves = 0, hmax = 0;
+  int32_t q = 2, levels = 0;
+  std::vector<int64_t> items;  // items per level; items[0] = leaves
+  // Device workspace (owned unless external).
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = true;
+  void* leafR = nullptr;
+  void* leafTau = nullptr;
+  void* leafT = nullptr;
+  std::vector<void*> nodeR, nodeY, nodeTau, nodeT;  // index l-1 for level l
+  void* d = nullptr;
+  int* status = nullptr;
+  // The factored matrix (borrowed).
+  void* A = nullptr;
+  int64_t lda = 0;
+  bool factored = false;
+  // Stage timing (tracing).
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events[TSQR_NUM_STAGES];
+  int64_t launches[TSQR_NUM_STAGES] = {0, 0, 0, 0};
+};
+
+struct caqr_q_s {
+  uint32_t magic = kCaqrMagic;
+  int32_t prec = TSQR_PREC_FP64;
+  size_t es = 8;
+  int64_t m = 0, n = 0, b = 0;
+  void* A = nullptr;
+  int64_t lda = 0;
+  unsigned char* ws = nullptr;
+  std::vector<tsqr_q_t> panels;
+  int* status = nullptr;  // panel 0's status word
+};
+
+namespace {
+
+bool valid(const tsqr_q_s* q) { return q && q->magic == kTsqrMagic; }
+
+// Records a CUDA event pair around one stage of a call when timing is on.
+struct StageTimer {
+  tsqr_q_s* q;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  StageTimer(const tsqr_q_s* qq, int st, cudaStream_t ss) : q(const_cast<tsqr_q_s*>(qq)), stage(st), s(ss) {
+    if (q->timing && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
+      cudaEventRecord(e0, s);
+  }
+  void stop(int64_t nlaunch) {
+    q->launches[stage] += nlaunch;
+    if (e1) {
+      cudaEventRecord(e1, s);
+      q->events[stage].emplace_back(e0, e1);
+      e0 = e1 = nullptr;
+    }
+  }
+  ~StageTimer() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+void clear_events(tsqr_q_s* q) {
+  for (auto& v : q->events) {
+    for (auto& p : v) {
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    v.clear();
+  }
+  for (auto& l : q->launches) l = 0;
+}
+bool valid(const caqr_q_s* q) { return q && q->magic == kCaqrMagic; }
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? TSQR_OK : (e == cudaErrorMemoryAllocation ? TSQR_ERR_NOMEM : TSQR_ERR_CUDA); }
+
+// Leaf partition (Section 2.1, 1-D block rows; the remainder rule is the
+// build's reading of the paper's "m_i >= n"): leaves of h rows, the last one
+// takes what is left and is merged into its predecessor when it would have
+// fewer than n rows.
+int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t* opts) {
+  if (opts && opts->flags != 0) return -4;
+  q->prec = prec;
+  q->es = prec == TSQR_PREC_FP64 ? 8 : 4;
+  q->m = m;
+  q->n = n;
+  const int64_t smax = max_smem_optin();
+  int64_t h = opts && opts->leaf_rows > 0 ? opts->leaf_rows : 0;
+  if (h == 0) {
+    // Largest multiple of 32 (at most 256 for FP64, 512 for FP32) whose leaf
+    // tile, plus a merged remainder of up to n-1 rows, fits in shared memory.
+    const int64_t cap = q->es == 8 ? 256 : 512;
+    int64_t fit = (smax - 8 * 1024) / (int64_t)(n * q->es) - (n - 1);
+    h = fit < cap ? fit : cap;
+    h = h / 32 * 32;
+    if (h < n) h = n;
+  }
+  if (h < n) return -4;
+  int64_t nl = (m + h - 1) / h;
+  if (nl < 1) nl = 1;
+  const int64_t rem = m - (nl - 1) * h;
+  if (nl > 1 && rem < n) --nl;
+  q->h = h;
+  q->nleaves = nl;
+  q->hmax = nl > 1 ? (m - (nl - 1) * h > h ? m - (nl - 1) * h : h) : m;
+  q->q = opts && opts->arity > 0 ? opts->arity : 2;
+  if (q->q < 2 || q->q > 16) return -4;
+  q->items.assign(1, nl);
+  while (q->items.back() > 1) q->items.push_back((q->items.back() + q->q - 1) / q->q);
+  q->levels = (int32_t)q->items.size() - 1;
+  if (n > kMaxN) return TSQR_ERR_UNSUPPORTED;
+  if ((int64_t)leaf_factor_smem((int)n, leaf_factor_ld((int)q->hmax), q->es) > smax) return TSQR_ERR_UNSUPPORTED;
+  if ((int64_t)leaf_apply_smem((int)n, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
+  if (q->levels > 0) {
+    if ((int64_t)node_factor_smem((int)n, q->q, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
+    if ((int64_t)node_apply_smem((int)n, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
+  }
+  return TSQR_OK;
+}
+
+size_t workspace_bytes(const tsqr_q_s* q) {
+  const size_t nn = (size_t)q->n * q->n * q->es, nv = (size_t)q->n * q->es;
+  size_t b = 0;
+  b += align_up(q->nleaves * nn) * 2 + align_up(q->nleaves * nv);
+  for (int l = 1; l <= q->levels; ++l) {
+    const size_t it = (size_t)q->items[l];
+    b += align_up(it * nn) * 2 + align_up(it * (q->q - 1) * nn) + align_up(it * nv);
+  }
+  b += align_up(nv) + align_up(sizeof(int));
+  return b;
+}
+
+void bind_workspace(tsqr_q_s* q, unsigned char* base) {
+  const size_t nn = (size_t)q->n * q->n * q->es, nv = (size_t)q->n * q->es;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    void* p = base + off;
+    off += align_up(bytes);
+    return p;
+  };
+  q->ws = base;
+  q->leafR = take(q->nleaves * nn);
+  q->leafT = take(q->nleaves * nn);
+  q->leafTau = take(q->nleaves * nv);
+  q->nodeR.assign(q->levels, nullptr);
+  q->nodeY.assign(q->levels, nullptr);
+  q->nodeTau.assign(q->levels, nullptr);
+  q->nodeT.assign(q->levels, nullptr);
+  for (int l = 1; l <= q->levels; ++l) {
+    const size_t it = (size_t)q->items[l];
+    q->nodeR[l - 1] = take(it * nn);
+    q->nodeT[l - 1] = take(it * nn);
+    q->nodeY[l - 1] = take(it * (q->q - 1) * nn);
+    q->nodeTau[l - 1] = take(it * nv);
+  }
+  q->d = take(nv);
+  q->status = (int*)take(sizeof(int));
+  q->ws_bytes = off;
+}
+
+void* root_r(const tsqr_q_s* q) { return q->levels == 0 ? q->leafR : q->nodeR[q->levels - 1]; }
+
+int64_t slot_stride(const tsqr_q_s* q, int level) {
+  int64_t s = q->h;
+  for (int l = 1; l < level; ++l) s *= q->q;
+  return s;
+}
+
+template <typename T>
+cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
+  LeafFactorArgs<T> la{};
+  la.A = A;
+  la.lda = lda;
+  la.m = q->m;
+  la.n = (int)q->n;
+  la.h = q->h;
+  la.nleaves = q->nleaves;
+  la.ld_s = leaf_factor_ld((int)q->hmax);
+  la.R = (T*)q->leafR;
+  la.tau = (T*)q->leafTau;
+  la.Tw = (T*)q->leafT;
+  la.status = q->status;
+  StageTimer t0(q, TSQR_STAGE_LEAF_FACTOR, s);
+  cudaError_t e = launch_leaf_factor(la, s);
+  if (e != cudaSuccess) return e;
+  t0.stop(1);
+  StageTimer t1(q, TSQR_STAGE_TREE_FACTOR, s);
+  for (int l = 1; l <= q->levels; ++l) {
+    NodeFactorArgs<T> na{};
+    na.Rin = (const T*)(l == 1 ? q->leafR : q->nodeR[l - 2]);
+    na.nin = q->items[l - 1];
+    na.arity = q->q;
+    na.n = (int)q->n;
+    na.nodes = q->items[l];
+    na.Rout = (T*)q->nodeR[l - 1];
+    na.Y = (T*)q->nodeY[l - 1];
+    na.tau = (T*)q->nodeTau[l - 1];
+    na.Tw = (T*)q->nodeT[l - 1];
+    na.status = q->status;
+    e = launch_node_factor(na, s);
+    if (e != cudaSuccess) return e;
+  }
+  e = launch_sign_fix((const T*)root_r(q), (int)q->n, (T*)q->d, R, ldr, zero_lower, s);
+  if (e == cudaSuccess) t1.stop(q->levels + 1);
+  return e;
+}
+
+template <typename T>
+cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  LeafApplyArgs<T> la{};
+  la.Y = (const T*)q->A;
+  la.ldy = q->lda;
+  la.m = q->m;
+  la.n = (int)q->n;
+  la.h = q->h;
+  la.nleaves = q->nleaves;
+  la.Tw = (const T*)q->leafT;
+  la.C = C;
+  la.ldc = ldc;
+  la.k = k;
+  auto node = [&](int l, int md) {
+    NodeApplyArgs<T> na{};
+    na.Y = (const T*)q->nodeY[l - 1];
+    na.Tw = (const T*)q->nodeT[l - 1];
+    na.nin = q->items[l - 1];
+    na.arity = q->q;
+    na.n = (int)q->n;
+    na.nodes = q->items[l];
+    na.slot_stride = slot_stride(q, l);
+    na.C = C;
+    na.ldc = ldc;
+    na.k = k;
+    na.mode = md;
+    return launch_node_apply(na, s);
+  };
+  auto leaf = [&](int md) {
+    StageTimer t(q, TSQR_STAGE_LEAF_APPLY, s);
+    la.mode = md;
+    cudaError_t r = launch_leaf_apply(la, s);
+    if (r == cudaSuccess) t.stop(1);
+    return r;
+  };
+  if (mode == kApplyQT) {
+    if ((e = leaf(kApplyQT)) != cudaSuccess) return e;
+    StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
+    for (int l = 1; l <= q->levels; ++l)
+      if ((e = node(l, kApplyQT)) != cudaSuccess) return e;
+    e = launch_scale_rows(C, ldc, (int)q->n, k, (const T*)q->d, s);
+    if (e == cudaSuccess) t.stop(q->levels + 1);
+    return e;
+  }
+  if (mode == kApplyQ) {
+    {
+      StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
+      if ((e = launch_scale_rows(C, ldc, (int)q->n, k, (const T*)q->d, s)) != cudaSuccess) return e;
+      for (int l = q->levels; l >= 1; --l)
+        if ((e = node(l, kApplyQ)) != cudaSuccess) return e;
+      t.stop(q->levels + 1);
+    }
+    return leaf(kApplyQ);
+  }
+  // Form the thin Q: the root slot starts as diag(d), every other row is
+  // produced top-down without being read.
+  {
+    StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
+    if ((e = launch_init_form(C, ldc, (int)q->n, (const T*)q->d, s)) != cudaSuccess) return e;
+    for (int l = q->levels; l >= 1; --l)
+      if ((e = node(l, kApplyForm)) != cudaSuccess) return e;
+    t.stop(q->levels + 1);
+  }
+  return leaf(kApplyForm);
+}
+
+int create_handle(int64_t m, int64_t n, int32_t prec, const tsqr_opts_t* opts, tsqr_q_t* out, unsigned char* external,
+                  cudaStream_t s) {
+  tsqr_q_s* q = new (std::nothrow) tsqr_q_s();
+  if (!q) return TSQR_ERR_NOMEM;
+  int rc = make_plan(q, m, n, prec, opts);
+  if (rc != TSQR_OK) {
+    delete q;
+    return rc;
+  }
+  if (external) {
+    q->owns_ws = false;
+    bind_workspace(q, external);
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, workspace_bytes(q));
+    if (e != cudaSuccess) {
+      delete q;
+      return cuda_err(e);
+    }
+    bind_workspace(q, (unsigned char*)p);
+  }
+  cudaError_t e = cudaMemsetAsync(q->status, 0, sizeof(int), s);
+  if (e != cudaSuccess) {
+    if (q->owns_ws) cudaFree(q->ws);
+    delete q;
+    return cuda_err(e);
+  }
+  *out = q;
+  return TSQR_OK;
+}
+
+int refactor(tsqr_q_s* q, void* A, int64_t lda, void* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
+  cudaError_t e;
+  if (q->prec == TSQR_PREC_FP64)
+    e = run_factor<double>(q, (double*)A, lda, (double*)R, ldr, zero_lower, s);
+  else
+    e = run_factor<float>(q, (float*)A, lda, (float*)R, ldr, zero_lower, s);
+  if (e != cudaSuccess) return cuda_err(e);
+  q->A = A;
+  q->lda = lda;
+  q->factored = true;
+  return TSQR_OK;
+}
+
+int destroy_handle(tsqr_q_s* q) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  q->magic = 0;
+  cudaError_t e = cudaSuccess;
+  if (q->owns_ws && q->ws) e = cudaFree(q->ws);
+  clear_events(q);
+  delete q;
+  return cuda_err(e);
+}
+
+int read_status(int* status, cudaStream_t s) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_err(e);
+  if (h & kStatusTimeout) return TSQR_ERR_TIMEOUT;
+  if (h & kStatusNonfinite) return TSQR_ERR_NONFINITE;
+  return TSQR_OK;
+}
+
+template <typename T>
+int factor_common(int64_t m, int64_t n, T* A, int64_t lda, T* R, int64_t ldr, const tsqr_opts_t* opts, tsqr_q_t* q,
+                  cudaStream_t s, int32_t prec) {
+  if (q) *q = nullptr;
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (m > 0 && n > 0 && !A) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (m > 0 && n > 0 && !R) return -5;
+  if (ldr < (n > 1 ? n : 1)) return -6;
+  if (m == 0 || n == 0) return TSQR_OK;
+  tsqr_q_t h = nullptr;
+  int rc = create_handle(m, n, prec, opts, &h, nullptr, s);
+  if (rc != TSQR_OK) return rc == -4 ? -7 : rc;
+  rc = refactor(h, A, lda, R, ldr, true, s);
+  if (rc != TSQR_OK || !q) {
+    if (!q) cudaStreamSynchronize(s);
+    destroy_handle(h);
+    return rc;
+  }
+  *q = h;
+  return TSQR_OK;
+}
+
+int apply_common(tsqr_q_s* q, int mode, int64_t k, void* C, int64_t ldc, cudaStream_t s) {
+  if (!valid(q) || !q->factored) return TSQR_ERR_HANDLE;
+  if (k < 0) return -2;
+  if (k == 0) return TSQR_OK;
+  if (!C) return -3;
+  if (ldc < q->m) return -4;
+  cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, mode, k, (double*)C, ldc, s)
+                                            : run_apply<float>(q, mode, k, (float*)C, ldc, s);
+  return cuda_err(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsqr_factor(int64_t m, int64_t n, double* A, int64_t lda, double* R, int64_t ldr, const tsqr_opts_t* opts,
+                tsqr_q_t* q, tsqr_stream_t stream) {
+  return factor_common<double>(m, n, A, lda, R, ldr, opts, q, (cudaStream_t)stream, TSQR_PREC_FP64);
+}
+
+int tsqr_factor_f32(int64_t m, int64_t n, float* A, int64_t lda, float* R, int64_t ldr, const tsqr_opts_t* opts,
+                    tsqr_q_t* q, tsqr_stream_t stream) {
+  return factor_common<float>(m, n, A, lda, R, ldr, opts, q, (cudaStream_t)stream, TSQR_PREC_FP32);
+}
+
+int tsqr_q_create(int64_t m, int64_t n, int32_t precision, const tsqr_opts_t* opts, tsqr_q_t* q,
+                  tsqr_stream_t stream) {
+  if (!q) return -5;
+  *q = nullptr;
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (precision != TSQR_PREC_FP64 && precision != TSQR_PREC_FP32) return -3;
+  return create_handle(m, n, precision, opts, q, nullptr, (cudaStream_t)stream);
+}
+
+int tsqr_refactor(tsqr_q_t q, void* A, int64_t lda, void* R, int64_t ldr, tsqr_stream_t stream) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (!A) return -2;
+  if (lda < q->m) return -3;
+  if (!R) return -4;
+  if (ldr < q->n) return -5;
+  return refactor(q, A, lda, R, ldr, true, (cudaStream_t)stream);
+}
+
+int tsqr_apply_qt(tsqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream) {
+  return apply_common(q, kApplyQT, k, C, ldc, (cudaStream_t)stream);
+}
+
+int tsqr_apply_q(tsqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream) {
+  return apply_common(q, kApplyQ, k, C, ldc, (cudaStream_t)stream);
+}
+
+int tsqr_form_q(tsqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream) {
+  if (!valid(q) || !q->factored) return TSQR_ERR_HANDLE;
+  if (!Q) return -2;
+  if (ldq < q->m) return -3;
+  if (Q == q->A) return -2;
+  cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, kApplyForm, q->n, (double*)Q, ldq, (cudaStream_t)stream)
+                                            : run_apply<float>(q, kApplyForm, q->n, (float*)Q, ldq, (cudaStream_t)stream);
+  return cuda_err(e);
+}
+
+int tsqr_sync_status(tsqr_q_t q, tsqr_stream_t stream) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  return read_status(q->status, (cudaStream_t)stream);
+}
+
+int tsqr_q_info(tsqr_q_t q, int64_t* m, int64_t* n, int32_t* precision, int64_t* leaves, int64_t* leaf_rows,
+                int32_t* arity, int32_t* levels) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (m) *m = q->m;
+  if (n) *n = q->n;
+  if (precision) *precision = q->prec;
+  if (leaves) *leaves = q->nleaves;
+  if (leaf_rows) *leaf_rows = q->h;
+  if (arity) *arity = q->q;
+  if (levels) *levels = q->levels;
+  return TSQR_OK;
+}
+
+int tsqr_q_destroy(tsqr_q_t q) { return destroy_handle(q); }
+
+int tsqr_q_set_timing(tsqr_q_t q, int32_t enable) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (enable) clear_events(q);
+  q->timing = enable != 0;
+  return TSQR_OK;
+}
+
+int tsqr_q_stage_times(tsqr_q_t q, double* ms, int64_t* launches, int32_t count) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (count < 0 || count > TSQR_NUM_STAGES) return -4;
+  for (int st = 0; st < count; ++st) {
+    double tot = 0.0;
+    for (auto& p : q->events[st]) {
+      cudaError_t e = cudaEventSynchronize(p.second);
+      if (e != cudaSuccess) return cuda_err(e);
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, p.first, p.second);
+      if (e != cudaSuccess) return cuda_err(e);
+      tot += t;
+    }
+    if (ms) ms[st] = tot;
+    if (launches) launches[st] = q->launches[st];
+  }
+  return TSQR_OK;
+}
+
+// ------------------------------------------------------------------ CAQR --
+
+int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
+                const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (q) *q = nullptr;
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (m > 0 && n > 0 && !A) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (b < 1) return -5;
+  if (update_precision != TSQR_PREC_FP64) return -6;
+  if (m == 0 || n == 0) return TSQR_OK;
+  caqr_q_s* c = new (std::nothrow) caqr_q_s();
+  if (!c) return TSQR_ERR_NOMEM;
+  c->m = m;
+  c->n = n;
+  c->b = b;
+  c->A = A;
+  c->lda = lda;
+  // Plan every panel, then one allocation for all of their workspaces.
+  std::vector<tsqr_q_s*> plans;
+  size_t total = 0;
+  int rc = TSQR_OK;
+  for (int64_t j0 = 0; j0 < n && rc == TSQR_OK; j0 += b) {
+    const int64_t jb = (n - j0) < b ? (n - j0) : b;
+    tsqr_q_s* p = new (std::nothrow) tsqr_q_s();
+    if (!p) {
+      rc = TSQR_ERR_NOMEM;
+      break;
+    }
+    rc = make_plan(p, m - j0, jb, TSQR_PREC_FP64, opts);
+    if (rc == -4) rc = -7;
+    plans.push_back(p);
+    total += workspace_bytes(p);
+  }
+  void* base = nullptr;
+  if (rc == TSQR_OK) rc = cuda_err(cudaMalloc(&base, total));
+  if (rc != TSQR_OK) {
+    for (auto* p : plans) delete p;
+    delete c;
+    return rc;
+  }
+  c->ws = (unsigned char*)base;
+  size_t off = 0;
+  for (auto* p : plans) {
+    p->owns_ws = false;
+    bind_workspace(p, c->ws + off);
+    off += workspace_bytes(p);
+    c->panels.push_back(p);
+  }
+  c->status = c->panels[0]->status;
+  for (auto* p : c->panels) {
+    cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
+    if (e != cudaSuccess) rc = cuda_err(e);
+  }
+  // Right-looking loop: TSQR of panel j, then (Q_j D_j)^T on the trailing columns.
+  for (size_t j = 0; j < c->panels.size() && rc == TSQR_OK; ++j) {
+    tsqr_q_s* p = c->panels[j];
+    const int64_t j0 = (int64_t)j * b;
+    double* P = A + j0 + j0 * lda;
+    rc = refactor(p, P, lda, P, lda, false, s);
+    const int64_t kt = n - j0 - p->n;
+    if (rc == TSQR_OK && kt > 0) rc = apply_common(p, kApplyQT, kt, A + j0 + (j0 + p->n) * lda, lda, s);
+  }
+  if (rc != TSQR_OK || !q) {
+    cudaStreamSynchronize(s);
+    caqr_q_destroy(c);
+    return rc;
+  }
+  *q = c;
+  return TSQR_OK;
+}
+
+int caqr_apply_qt(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (k < 0) return -2;
+  if (k == 0) return TSQR_OK;
+  if (!C) return -3;
+  if (ldc < q->m) return -4;
+  for (size_t j = 0; j < q->panels.size(); ++j) {
+    const int64_t j0 = (int64_t)j * q->b;
+    int rc = apply_common(q->panels[j], kApplyQT, k, (double*)C + j0, ldc, (cudaStream_t)stream);
+    if (rc != TSQR_OK) return rc;
+  }
+  return TSQR_OK;
+}
+
+int caqr_apply_q(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (k < 0) return -2;
+  if (k == 0) return TSQR_OK;
+  if (!C) return -3;
+  if (ldc < q->m) return -4;
+  for (size_t j = q->panels.size(); j-- > 0;) {
+    const int64_t j0 = (int64_t)j * q->b;
+    int rc = apply_common(q->panels[j], kApplyQ, k, (double*)C + j0, ldc, (cudaStream_t)stream);
+    if (rc != TSQR_OK) return rc;
+  }
+  return TSQR_OK;
+}
+
+int caqr_form_q(caqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (!Q) return -2;
+  if (ldq < q->m) return -3;
+  if (Q == q->A) return -2;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Q = Q_0 diag(I, Q_1) diag(I, Q_2) ... [I_n; 0]: start from [I_n; 0] and
+  // apply the panels last to first, each to the columns it can reach.
+  cudaError_t e = cudaMemset2DAsync(Q, ldq * sizeof(double), 0, q->m * sizeof(double), q->n, s);
+  if (e != cudaSuccess) return cuda_err(e);
+  e = launch_init_form<double>((double*)Q, ldq, (int)q->n, nullptr, s);
+  if (e != cudaSuccess) return cuda_err(e);
+  for (size_t j = q->panels.size(); j-- > 0;) {
+    const int64_t j0 = (int64_t)j * q->b;
+    int rc = apply_common(q->panels[j], kApplyQ, q->n - j0, (double*)Q + j0 + j0 * ldq, ldq, s);
+    if (rc != TSQR_OK) return rc;
+  }
+  return TSQR_OK;
+}
+
+int caqr_sync_status(caqr_q_t q, tsqr_stream_t stream) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  int worst = TSQR_OK;
+  for (auto* p : q->panels) {
+    int rc = read_status(p->status, (cudaStream_t)stream);
+    if (rc != TSQR_OK) worst = rc;
+  }
+  return worst;
+}
+
+int caqr_q_destroy(caqr_q_t q) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  q->magic = 0;
+  for (auto* p : q->panels) destroy_handle(p);
+  cudaError_t e = q->ws ? cudaFree(q->ws) : cudaSuccess;
+  delete q;
+  return cuda_err(e);
+}
+
+const char* tsqr_status_string(int code) {
+  if (code < 0) return "invalid argument";
+  switch (code) {
+    case TSQR_OK: return "ok";
+    case TSQR_ERR_CUDA: return "CUDA runtime error";
+    case TSQR_ERR_NOMEM: return "device allocation failed";
+    case TSQR_ERR_TIMEOUT: return "device-side wait timed out";
+    case TSQR_ERR_NONFINITE: return "non-finite value in a column norm or pivot";
+    case TSQR_ERR_UNSUPPORTED: return "unsupported shape or precision";
+    case TSQR_ERR_HANDLE: return "invalid handle";
+    default: return "unknown status";
+  }
+}
+
+int tsqr_version(void) { return 100; }
+
+}  // extern "C"

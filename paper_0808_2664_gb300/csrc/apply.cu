@@ -1,0 +1,401 @@
+// Implicit application of the tree-structured Q (Section 2.1,
+// Eq. TSQR_binarytree_4): Q = diag(Q_i) * (tree-node factors) * D.
+//
+// Every factor is a compact-WY block reflector I - Y T Y^T (Schreiber and Van
+// Loan, cited in Section 2.1).  A leaf applies it to its h-row block of C:
+//   W = Y^T C,  W <- T^T W (for Q^T) or T W (for Q),  C <- C - Y W.
+// A tree node applies it to the q stacked n-row "slots" of C that hold its
+// children's R rows; its Y is [I; Y_1; ...; Y_{q-1}] with upper-triangular Y_b.
+// The "form" mode computes Q [X; 0] reading only X (the first n rows), which
+// is how the thin Q is built top-down without initialising the rest of Q.
+#include <cuda_runtime.h>
+
+#include "tsqr_internal.cuh"
+
+namespace tsqr {
+namespace {
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
+
+// ---------------------------------------------------------------- leaves --
+// Shared memory: Ys [kApplyRows][n+1] (row-major), Cs [kApplyRows][kc+1],
+// Ws [n][kc] (W, then T-times-W), Ts [n][n] (column-major T).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int RB = kApplyRows;
+  constexpr int KC = kApplyCols;
+  const int n = a.n;
+  const int ly = n + 1, lc = KC + 1;
+  T* Ys = reinterpret_cast<T*>(smem);
+  T* Cs = reinterpret_cast<T*>(smem + align16(sizeof(T) * RB * ly));
+  T* Ws = reinterpret_cast<T*>(smem + align16(sizeof(T) * RB * ly) + align16(sizeof(T) * RB * lc));
+  T* Ts = Ws + (size_t)n * KC;
+  const int tid = threadIdx.x;
+
+  const int64_t leaf = blockIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.y * KC;
+  const int kc = (int)((a.k - k0) < KC ? (a.k - k0) : KC);
+  const int64_t r0 = leaf * a.h;
+  const int hl = (leaf == a.nleaves - 1) ? (int)(a.m - r0) : (int)a.h;
+  const T* Yg = a.Y + r0;
+  T* Cg = a.C + r0 + k0 * a.ldc;
+  const int mode = a.mode;
+  const int rows1 = mode == kApplyForm ? n : hl;  // rows that feed W
+
+  // T of this leaf (column-major n x n).
+  const T* Tg = a.Tw + leaf * (int64_t)n * n;
+  for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
+
+  // Phase 1: W = Y^T C over rows1 rows; 4x4 register tiles of W.
+  const int tp = (n + 3) / 4, tcn = (kc + 3) / 4;
+  const int ntiles = tp * tcn;
+  T acc[2][4][4];
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[t][x][y] = T(0);
+
+  for (int rb = 0; rb < rows1; rb += RB) {
+    __syncthreads();
+    for (int idx = tid; idx < RB * n; idx += NT) {
+      const int i = idx % RB, p = idx / RB;
+      const int r = rb + i;
+      T v = T(0);
+      if (r < rows1) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
+      Ys[i * ly + p] = v;
+    }
+    for (int idx = tid; idx < RB * KC; idx += NT) {
+      const int i = idx % RB, c = idx / RB;
+      const int r = rb + i;
+      Cs[i * lc + c] = (r < rows1 && c < kc) ? Cg[r + (int64_t)c * a.ldc] : T(0);
+    }
+    __syncthreads();
+    const int rmax = min(RB, rows1 - rb);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int tile = tid + t * NT;
+      if (tile >= ntiles) break;
+      const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
+      for (int i = 0; i < rmax; ++i) {
+        T yv[4], cv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) yv[x] = (p0 + x < n) ? Ys[i * ly + p0 + x] : T(0);
+#pragma unroll
+        for (int y = 0; y < 4; ++y) cv[y] = Cs[i * lc + c0 + y];
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[t][x][y] = fma(yv[x], cv[y], acc[t][x][y]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int tile = tid + t * NT;
+    if (tile >= ntiles) break;
+    const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+        if (p0 + x < n && c0 + y < KC) Ws[(p0 + x) * KC + c0 + y] = acc[t][x][y];
+  }
+  __syncthreads();
+
+  // Phase 2: W <- T^T W (Q^T) or T W (Q, form).
+  const bool trans = mode == kApplyQT;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int tile = tid + t * NT;
+    if (tile >= ntiles) break;
+    const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int p = p0 + x;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[t][x][y] = T(0);
+      if (p >= n) continue;
+      // T^T(p, q) = T(q, p), nonzero for q <= p; T(p, q) nonzero for q >= p.
+      const int qa = trans ? 0 : p, qb = trans ? p : n - 1;
+      for (int qq = qa; qq <= qb; ++qq) {
+        const T tv = trans ? Ts[qq + p * n] : Ts[p + qq * n];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[t][x][y] = fma(tv, Ws[qq * KC + c0 + y], acc[t][x][y]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int tile = tid + t * NT;
+    if (tile >= ntiles) break;
+    const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y)
+        if (p0 + x < n && c0 + y < KC) Ws[(p0 + x) * KC + c0 + y] = acc[t][x][y];
+  }
+
+  // Phase 3: C <- C - Y W  (form: C <- [X; 0] - Y W).  Thread = (row, column group).
+  constexpr int CG = NT / RB;
+  const int i = tid % RB, cg = tid / RB;
+  for (int rb = 0; rb < hl; rb += RB) {
+    __syncthreads();
+    for (int idx = tid; idx < RB * n; idx += NT) {
+      const int ii = idx % RB, p = idx / RB;
+      const int r = rb + ii;
+      T v = T(0);
+      if (r < hl) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
+      Ys[ii * ly + p] = v;
+    }
+    __syncthreads();
+    const int r = rb + i;
+    if (r < hl) {
+      const int pmax = min(n, r + 1);  // Y(r, p) = 0 for p > r
+      for (int c = cg; c < kc; c += CG) {
+        T s = T(0);
+        for (int p = 0; p < pmax; ++p) s = fma(Ys[i * ly + p], Ws[p * KC + c], s);
+        T* dst = Cg + r + (int64_t)c * a.ldc;
+        const T old = (mode == kApplyForm && r >= n) ? T(0) : *dst;
+        *dst = old - s;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- nodes --
+// Shared memory (column-major tiles, ldn odd): B1 [kc][ldn] holds a lower
+// slot while W accumulates and then W' = T^(T) W; B2 [kc][ldn] holds W and
+// later Y_b W'; Ys [n][ldn] one lower block of Y; Ts [n][n].
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int KC = kApplyCols;
+  const int n = a.n, q = a.arity;
+  const int ldn = n | 1;
+  T* B1 = reinterpret_cast<T*>(smem);
+  T* B2 = B1 + (size_t)KC * ldn;
+  T* Ys = B2 + (size_t)KC * ldn;
+  T* Ts = Ys + (size_t)n * ldn;
+  const int tid = threadIdx.x;
+  const int64_t node = blockIdx.x;
+  const int64_t c0 = node * q;
+  const int nc = (int)((a.nin - c0) < q ? (a.nin - c0) : q);
+  if (nc <= 1) return;  // a lone child: identity
+  const int64_t k0 = (int64_t)blockIdx.y * KC;
+  const int kc = (int)((a.k - k0) < KC ? (a.k - k0) : KC);
+  const int64_t nn = (int64_t)n * n;
+  const T* Yn = a.Y + node * (int64_t)(q - 1) * nn;
+  const T* Tg = a.Tw + node * nn;
+  const int mode = a.mode;
+  const bool trans = mode == kApplyQT;
+  auto slot_ptr = [&](int b) -> T* { return a.C + (c0 + b) * a.slot_stride + k0 * a.ldc; };
+  auto load_y = [&](int b) {
+    const T* Yb = Yn + (int64_t)(b - 1) * nn;
+    for (int idx = tid; idx < n * n; idx += NT) {
+      const int i = idx % n, p = idx / n;
+      Ys[p * ldn + i] = Yb[idx];
+    }
+  };
+
+  for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
+  {  // W = C_0 (form: X)
+    const T* src = slot_ptr(0);
+    for (int idx = tid; idx < n * kc; idx += NT) {
+      const int i = idx % n, c = idx / n;
+      B2[c * ldn + i] = src[i + (int64_t)c * a.ldc];
+    }
+  }
+  constexpr int PG = NT / KC;
+  const int cc = tid % KC, pg = tid / KC;
+  if (mode != kApplyForm) {
+    // W += Y_b^T C_b; Y_b is upper triangular, so W(p) sums rows i <= p.
+    for (int b = 1; b < nc; ++b) {
+      __syncthreads();
+      const T* src = slot_ptr(b);
+      for (int idx = tid; idx < n * kc; idx += NT) {
+        const int i = idx % n, c = idx / n;
+        B1[c * ldn + i] = src[i + (int64_t)c * a.ldc];
+      }
+      load_y(b);
+      __syncthreads();
+      if (cc < kc) {
+        for (int p = pg; p < n; p += PG) {
+          T s = B2[cc * ldn + p];
+          for (int i = 0; i <= p; ++i) s = fma(Ys[p * ldn + i], B1[cc * ldn + i], s);
+          B2[cc * ldn + p] = s;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // W' = T^T W (Q^T) or T W (Q, form), into B1.
+  if (cc < kc) {
+    for (int p = pg; p < n; p += PG) {
+      T s = T(0);
+      if (trans) {
+        for (int qq = 0; qq <= p; ++qq) s = fma(Ts[qq + p * n], B2[cc * ldn + qq], s);
+      } else {
+        for (int qq = p; qq < n; ++qq) s = fma(Ts[p + qq * n], B2[cc * ldn + qq], s);
+      }
+      B1[cc * ldn + p] = s;
+    }
+  }
+  __syncthreads();
+  {  // C_0 <- C_0 - W'  (form: X - W')
+    T* dst = slot_ptr(0);
+    for (int idx = tid; idx < n * kc; idx += NT) {
+      const int i = idx % n, c = idx / n;
+      dst[i + (int64_t)c * a.ldc] -= B1[c * ldn + i];
+    }
+  }
+  // C_b <- C_b - Y_b W'  (form: -Y_b W').
+  for (int b = 1; b < nc; ++b) {
+    __syncthreads();
+    load_y(b);
+    __syncthreads();
+    if (cc < kc) {
+      for (int i = pg; i < n; i += PG) {
+        T s = T(0);
+        for (int p = i; p < n; ++p) s = fma(Ys[p * ldn + i], B1[cc * ldn + p], s);
+        B2[cc * ldn + i] = s;
+      }
+    }
+    __syncthreads();
+    T* dst = slot_ptr(b);
+    for (int idx = tid; idx < n * kc; idx += NT) {
+      const int i = idx % n, c = idx / n;
+      T* e = dst + i + (int64_t)c * a.ldc;
+      *e = (mode == kApplyForm ? T(0) : *e) - B2[c * ldn + i];
+    }
+  }
+}
+
+// ------------------------------------------------------------ utilities --
+template <typename T>
+__global__ void sign_fix_kernel(const T* Rroot, int n, T* d, T* Rout, int64_t ldr, bool zero_lower) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx % n, c = idx / n;
+    const T di = Rroot[i + (int64_t)i * n] < T(0) ? T(-1) : T(1);
+    if (i <= c) Rout[i + (int64_t)c * ldr] = di * Rroot[idx];
+    else if (zero_lower) Rout[i + (int64_t)c * ldr] = T(0);
+    if (c == 0) d[i] = di;
+  }
+}
+
+template <typename T>
+__global__ void scale_rows_kernel(T* C, int64_t ldc, int n, int64_t k, const T* d) {
+  const int64_t total = (int64_t)n * k;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n);
+    const int64_t c = idx / n;
+    C[i + c * ldc] *= d[i];
+  }
+}
+
+template <typename T>
+__global__ void init_form_kernel(T* Q, int64_t ldq, int n, const T* d) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx % n, c = idx / n;
+    Q[i + (int64_t)c * ldq] = i == c ? (d ? d[i] : T(1)) : T(0);
+  }
+}
+
+template <typename T>
+__global__ void copy_upper_kernel(const T* src, int n, T* dst, int64_t ldd) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx % n, c = idx / n;
+    dst[i + (int64_t)c * ldd] = i <= c ? src[idx] : T(0);
+  }
+}
+
+inline unsigned small_grid(int64_t work) {
+  int64_t g = (work + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 4096) g = 4096;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+size_t leaf_apply_smem(int n, size_t elem) {
+  return align16(elem * kApplyRows * (n + 1)) + align16(elem * kApplyRows * (kApplyCols + 1)) +
+         elem * (size_t)n * kApplyCols + elem * (size_t)n * n;
+}
+
+size_t node_apply_smem(int n, size_t elem) {
+  const int ldn = n | 1;
+  return elem * ((size_t)2 * kApplyCols * ldn + (size_t)n * ldn + (size_t)n * n);
+}
+
+template <typename T>
+cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s) {
+  if (a.nleaves <= 0 || a.k <= 0 || a.n <= 0) return cudaSuccess;
+  const size_t smem = leaf_apply_smem(a.n, sizeof(T));
+  auto kern = leaf_apply_kernel<T, kApplyThreads>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t kchunks = (a.k + kApplyCols - 1) / kApplyCols;
+  if (kchunks > 65535 || a.nleaves > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)a.nleaves, (unsigned)kchunks);
+  kern<<<grid, kApplyThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_node_apply(const NodeApplyArgs<T>& a, cudaStream_t s) {
+  if (a.nodes <= 0 || a.k <= 0 || a.n <= 0) return cudaSuccess;
+  const size_t smem = node_apply_smem(a.n, sizeof(T));
+  auto kern = node_apply_kernel<T, kApplyThreads>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t kchunks = (a.k + kApplyCols - 1) / kApplyCols;
+  if (kchunks > 65535 || a.nodes > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)a.nodes, (unsigned)kchunks);
+  kern<<<grid, kApplyThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sign_fix(const T* Rroot, int n, T* d, T* Rout, int64_t ldr, bool zero_lower, cudaStream_t s) {
+  sign_fix_kernel<T><<<small_grid((int64_t)n * n), 256, 0, s>>>(Rroot, n, d, Rout, ldr, zero_lower);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale_rows(T* C, int64_t ldc, int n, int64_t k, const T* d, cudaStream_t s) {
+  if (k <= 0 || n <= 0) return cudaSuccess;
+  scale_rows_kernel<T><<<small_grid((int64_t)n * k), 256, 0, s>>>(C, ldc, n, k, d);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_init_form(T* Q, int64_t ldq, int n, const T* d, cudaStream_t s) {
+  init_form_kernel<T><<<small_grid((int64_t)n * n), 256, 0, s>>>(Q, ldq, n, d);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_upper(const T* src, int n, T* dst, int64_t ldd, cudaStream_t s) {
+  copy_upper_kernel<T><<<small_grid((int64_t)n * n), 256, 0, s>>>(src, n, dst, ldd);
+  return cudaGetLastError();
+}
+
+#define TSQR_INSTANTIATE(T)                                                                          \
+  template cudaError_t launch_leaf_apply<T>(const LeafApplyArgs<T>&, cudaStream_t);                  \
+  template cudaError_t launch_node_apply<T>(const NodeApplyArgs<T>&, cudaStream_t);                  \
+  template cudaError_t launch_sign_fix<T>(const T*, int, T*, T*, int64_t, bool, cudaStream_t);       \
+  template cudaError_t launch_scale_rows<T>(T*, int64_t, int, int64_t, const T*, cudaStream_t);      \
+  template cudaError_t launch_init_form<T>(T*, int64_t, int, const T*, cudaStream_t);                \
+  template cudaError_t launch_copy_upper<T>(const T*, int, T*, int64_t, cudaStream_t);
+TSQR_INSTANTIATE(double)
+TSQR_INSTANTIATE(float)
+#undef TSQR_INSTANTIATE
+
+}  // namespace tsqr

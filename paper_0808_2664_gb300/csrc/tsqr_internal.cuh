@@ -1,0 +1,119 @@
+// Internal declarations shared by the TSQR / CAQR translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace tsqr {
+
+// Bits of the device status word.
+constexpr int kStatusNonfinite = 1;
+constexpr int kStatusTimeout = 2;
+
+// Threads per CTA of the factor and apply kernels.
+constexpr int kLeafThreads = 256;
+constexpr int kNodeThreads = 128;
+constexpr int kApplyThreads = 256;
+// Columns of C handled by one CTA of the apply kernels.
+constexpr int kApplyCols = 64;
+// Rows of a leaf staged per pass in the apply kernels.
+constexpr int kApplyRows = 32;
+// Largest n the kernels are built for.
+constexpr int kMaxN = 128;
+
+// Three apply modes: C <- Q^T C, C <- Q C, and "form": C <- Q [X; 0] where X
+// is read from the first n rows of the block and the rest of the block is
+// written without being read.
+enum ApplyMode : int { kApplyQT = 0, kApplyQ = 1, kApplyForm = 2 };
+
+// Leaf Householder QR of all row blocks of A (Section 2.1, Eq. TSQR_binarytree_1).
+template <typename T>
+struct LeafFactorArgs {
+  T* A;             // m x n, column-major; leaf rows overwritten with Y and R_i
+  int64_t lda;
+  int64_t m;        // total rows
+  int n;            // columns
+  int64_t h;        // nominal leaf height; leaf i starts at row i*h
+  int64_t nleaves;  // the last leaf runs to row m
+  int ld_s;         // shared-memory leading dimension of the leaf tile (odd)
+  T* R;             // nleaves x (n x n): leaf R factors, level-0 items of the tree
+  T* tau;           // nleaves x n
+  T* Tw;            // nleaves x (n x n): compact-WY T of each leaf
+  int* status;
+};
+
+// Structured QR of up to q stacked triangles per node (Section 2.1,
+// Eq. TSQR_binarytree_2): nodes of one tree level.
+template <typename T>
+struct NodeFactorArgs {
+  const T* Rin;     // items of the level below: nin x (n x n), upper triangular
+  int64_t nin;
+  int arity;        // q
+  int n;
+  int64_t nodes;    // ceil(nin / q)
+  T* Rout;          // nodes x (n x n)
+  T* Y;             // nodes x (q-1) x (n x n): upper-triangular reflector blocks
+  T* tau;           // nodes x n
+  T* Tw;            // nodes x (n x n)
+  int* status;
+};
+
+template <typename T>
+struct LeafApplyArgs {
+  const T* Y;       // the factored A: leaf Householder vectors
+  int64_t ldy;
+  int64_t m;
+  int n;
+  int64_t h;
+  int64_t nleaves;
+  const T* Tw;      // nleaves x (n x n)
+  T* C;             // m x k
+  int64_t ldc;
+  int64_t k;
+  int mode;         // ApplyMode
+};
+
+template <typename T>
+struct NodeApplyArgs {
+  const T* Y;       // nodes x (q-1) x (n x n)
+  const T* Tw;      // nodes x (n x n)
+  int64_t nin;      // items of the level below
+  int arity;
+  int n;
+  int64_t nodes;
+  int64_t slot_stride;  // rows between consecutive items of the level below
+  T* C;
+  int64_t ldc;
+  int64_t k;
+  int mode;
+};
+
+template <typename T>
+cudaError_t launch_leaf_factor(const LeafFactorArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_node_apply(const NodeApplyArgs<T>& a, cudaStream_t s);
+
+// d = sign(diag Rroot) (sign(0) = +1); Rout = D * triu(Rroot), ldr.  Entries
+// below the diagonal of Rout are zeroed when zero_lower, left alone otherwise.
+template <typename T>
+cudaError_t launch_sign_fix(const T* Rroot, int n, T* d, T* Rout, int64_t ldr, bool zero_lower, cudaStream_t s);
+// Rows 0..n-1 of C (k columns) scaled by d.
+template <typename T>
+cudaError_t launch_scale_rows(T* C, int64_t ldc, int n, int64_t k, const T* d, cudaStream_t s);
+// Q(0:n, 0:n) = diag(d) (the identity when d is null).
+template <typename T>
+cudaError_t launch_init_form(T* Q, int64_t ldq, int n, const T* d, cudaStream_t s);
+// Copy the n x n upper triangle of src (ld n) into dst (ldd), zero below.
+template <typename T>
+cudaError_t launch_copy_upper(const T* src, int n, T* dst, int64_t ldd, cudaStream_t s);
+
+// Shared-memory bytes the leaf factor kernel needs for a leaf of hmax rows.
+size_t leaf_factor_smem(int n, int hmax, size_t elem);
+int leaf_factor_ld(int hmax);
+
+}  // namespace tsqr
