@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--m", type=int, default=4194304)
     p.add_argument("--n", type=int, default=64)
-    p.add_argument("--leaf-rows", type=int, default=256)
+    p.add_argument("--leaf-rows", type=int, default=0, help="0 = the library default")
     p.add_argument("--arity", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-e2e", action="store_true")

@@ -138,12 +138,12 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
   const int64_t smax = max_smem_optin();
   int64_t h = opts && opts->leaf_rows > 0 ? opts->leaf_rows : 0;
   if (h == 0) {
-    // Largest multiple of 32 (at most 256 for FP64, 512 for FP32) whose leaf
-    // tile, plus a merged remainder of up to n-1 rows, fits in shared memory.
-    const int64_t cap = q->es == 8 ? 256 : 512;
-    int64_t fit = (smax - 8 * 1024) / (int64_t)(n * q->es) - (n - 1);
-    h = fit < cap ? fit : cap;
-    h = h / 32 * 32;
+    // Largest power of two (at most 1024) whose n-column leaf tile stays
+    // within about 68 KB, so that three leaf CTAs share an SM and hide each
+    // other's serial reflector steps.
+    const int64_t budget = 68 * 1024 / (int64_t)q->es;
+    h = 1;
+    while (h * 2 <= budget / n && h * 2 <= 1024) h *= 2;
     if (h < n) h = n;
   }
   if (h < n) return -4;

@@ -1,20 +1,24 @@
 // Leaf Householder QR of every row block of A (Section 2.1,
 // Eq. TSQR_binarytree_1: A_i = Q_i R_i for each block A_i).
 //
-// One CTA factors one leaf at a time (grid-stride over leaves).  The h x n
-// leaf sits in shared memory, column-major with an odd leading dimension so
-// that threads walking different columns at the same row hit different banks.
-// Per column j the CTA runs four phases separated by barriers:
-//   C  thread 0 turns (alpha, ||tail||^2) into (beta, tau, scale);
-//   S  the tail of column j is scaled into the Householder vector u_j;
-//   A  dot products of u_j with every other column: w_c = u_j^T a_c for c > j
-//      (the trailing update) and z_p = y_p^T u_j for p < j (the compact-WY T),
-//      rows split into groups whose partial sums meet by warp shuffles;
-//   B  a_c -= tau_j w_c u_j for c > j, and the squared norm of the next
-//      column's tail, accumulated while it is being updated.
+// One CTA factors one leaf at a time (grid-stride over leaves); several CTAs
+// share an SM so that one CTA's serial reflector step overlaps the others'
+// bulk updates.  The h x n leaf sits in shared memory, column-major with an
+// odd leading dimension so that threads walking different columns at the
+// same row hit different banks.  Per column j:
+//   C  one warp sums the partial squared norms of the tail, its lane 0 turns
+//      (alpha, ||tail||^2) into (beta, tau, scale), and the warp scales the
+//      tail into the Householder vector u_j (unit entry implicit);
+//   A  dot products w_c = u_j^T a_c for the trailing columns c > j, rows
+//      split into groups whose partial sums go to shared memory;
+//   B  a_c -= tau_j w_c u_j, and the squared norm of the next column's tail,
+//      accumulated while that column is updated.
 // Work is re-partitioned over all threads in every phase, so the shrinking
-// active block keeps the FP64 pipe busy.  Arithmetic: products in T (FP64, or
-// FP32 for the mixed form); norms, beta, tau and scale always in FP64.
+// active block keeps every warp busy.  After the last column, the
+// compact-WY T of the leaf is built from Z = strictly-upper(Y^T Y) (a
+// register-tiled product) and tau by a blocked doubling recurrence.
+// Arithmetic: products in T (FP64, or FP32 for the mixed form); norms, beta,
+// tau and scale always in FP64.
 #include <cuda_runtime.h>
 
 #include "reflector.cuh"
@@ -27,23 +31,28 @@ constexpr int kMinRows = 8;
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <typename T, int NT>
+// Bytes of the region that holds the leaf tile and, after write-back, the
+// FP64 T matrix plus the doubling workspace.
+__host__ __device__ inline size_t tile_region(int n, int ld, size_t elem) {
+  const size_t tile = align_up(elem * (size_t)n * ld, 16);
+  const size_t tm = align_up(sizeof(double) * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
+  return tile > tm ? tile : tm;
+}
+
+template <typename T, int NT, int NMAX>
 __global__ void __launch_bounds__(NT) leaf_factor_kernel(LeafFactorArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int n = a.n;
   const int ld = a.ld_s;
-  const int hmax_tile = ld;
   T* S = reinterpret_cast<T*>(smem);
-  size_t off = align_up(sizeof(T) * (size_t)n * hmax_tile, 16);
-  off = off > sizeof(double) * (size_t)n * n ? off : align_up(sizeof(double) * (size_t)n * n, 16);
-  double* part = reinterpret_cast<double*>(smem + off);  // NT partial dot products
-  double* nrm_part = part + NT;                           // NT partial squared norms
-  double* tau_s = nrm_part + NT;                          // n reflector scalars
-  double* Tm = reinterpret_cast<double*>(smem);           // reuses the tile after write-back
-  __shared__ double sh_scale;
+  double* part = reinterpret_cast<double*>(smem + tile_region(n, ld, sizeof(T)));  // NT partial dots
+  double* nrm_part = part + NT;                                                      // NT partial norms
+  double* tau_s = nrm_part + NT;                                                     // n
+  double* Tm = reinterpret_cast<double*>(smem);   // n x n, after write-back
+  double* Wt = Tm + (size_t)n * n;                // doubling workspace
   __shared__ int sh_nrg;
   const int tid = threadIdx.x;
-  const int lane = tid & 31;
+  const int lane = tid & 31, warp = tid >> 5;
 
   for (int64_t leaf = blockIdx.x; leaf < a.nleaves; leaf += gridDim.x) {
     const int64_t r0 = leaf * a.h;
@@ -66,122 +75,159 @@ __global__ void __launch_bounds__(NT) leaf_factor_kernel(LeafFactorArgs<T> a) {
     __syncthreads();
 
     for (int j = 0; j < n; ++j) {
-      // Phase C: reflector scalars for column j.
-      if (tid == 0) {
+      T* colj = S + j * ld;
+      // Phase C: reflector for column j, by one warp chosen round-robin so
+      // that the serial step does not always load the same SM sub-partition.
+      if (warp == (j % (NT / 32))) {
+        const int nrg = sh_nrg;
         double ssq = 0.0;
-        for (int g = 0; g < sh_nrg; ++g) ssq += nrm_part[g];
-        const T* col = S + j * ld;
-        const double alpha = (double)col[j];
-        const int len = hl - j - 1;
-        Reflector r = make_reflector(alpha, ssq,
-                                     [&]() { return scaled_norm(len, [&](int i) { return (double)col[j + 1 + i]; }); },
-                                     a.status);
-        tau_s[j] = r.tau;
-        sh_scale = r.scale;
-        S[j * ld + j] = (T)r.beta;
+        for (int g = lane; g < nrg; g += 32) ssq += nrm_part[g];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+        double scale = 0.0;
+        if (lane == 0) {
+          const double alpha = (double)colj[j];
+          const int len = hl - j - 1;
+          Reflector r = make_reflector(
+              alpha, ssq, [&]() { return scaled_norm(len, [&](int i) { return (double)colj[j + 1 + i]; }); },
+              a.status);
+          tau_s[j] = r.tau;
+          scale = r.scale;
+          colj[j] = (T)r.beta;
+        }
+        scale = __shfl_sync(0xffffffffu, scale, 0);
+        for (int i = j + 1 + lane; i < hl; i += 32) colj[i] = (T)((double)colj[i] * scale);
       }
       __syncthreads();
-      // Phase S: the tail of column j becomes u_j (unit entry implicit).
-      {
-        const double scale = sh_scale;
-        T* col = S + j * ld;
-        for (int i = j + 1 + tid; i < hl; i += NT) col[i] = (T)((double)col[i] * scale);
-      }
-      __syncthreads();
+      const int acols = n - 1 - j;
+      if (acols == 0) break;
       const int rows = hl - j;  // rows j .. hl-1
-      // Phase A: u_j^T a_c for every c != j.
-      const int acols = n - 1;
-      int rga = 1;
-      if (acols > 0) {
-        int lim = NT / acols;
+      int rg = NT / acols;
+      {
         int byrows = rows / kMinRows;
         if (byrows < 1) byrows = 1;
-        if (lim > byrows) lim = byrows;
-        if (lim > 32) lim = 32;
-        rga = pow2_floor(lim < 1 ? 1 : lim);
-        int chunk = (rows + rga - 1) / rga;
-        chunk |= 1;  // odd stride between the row groups of one warp
-        const int slot = tid / rga, g = tid % rga;
+        if (rg > byrows) rg = byrows;
+        if (rg < 1) rg = 1;
+      }
+      const int chunk = (rows + rg - 1) / rg;
+      const int slot = tid % acols, g = tid / acols;
+      const int c = j + 1 + slot;
+      int i0 = j + g * chunk;
+      const int i1 = min(i0 + chunk, hl);
+      // Phase A: partial dot products u_j^T a_c over this thread's rows.
+      if (g < rg) {
+        const T* cc = S + c * ld;
         T s = T(0);
-        if (slot < acols) {
-          const int c = slot < j ? slot : slot + 1;
-          const T* u = S + j * ld;
-          const T* cc = S + c * ld;
-          int i = j + g * chunk;
-          const int i1 = min(i + chunk, hl);
-          if (i == j && i < i1) {
-            s = cc[j];
-            ++i;
-          }
-          for (; i < i1; ++i) s = fma(u[i], cc[i], s);
+        int i = i0;
+        if (i == j && i < i1) {
+          s = cc[j];
+          ++i;
         }
-        // Reduce over the rga row groups of each slot (consecutive lanes).
-        for (int o = rga >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (slot < acols && g == 0) part[slot] = (double)s;
-        (void)lane;
+        for (; i < i1; ++i) s = fma(colj[i], cc[i], s);
+        part[g * acols + slot] = (double)s;
       }
       __syncthreads();
-      // Phase B: z for columns p < j (to the T buffer), updates for c > j.
-      if (tid < j) a.Tw[leaf * (int64_t)n * n + tid + (int64_t)j * n] = (T)part[tid];
-      const int bcols = n - 1 - j;
-      if (bcols > 0) {
-        int rgb = NT / bcols;
-        int byrows = rows / kMinRows;
-        if (byrows < 1) byrows = 1;
-        if (rgb > byrows) rgb = byrows;
-        if (rgb < 1) rgb = 1;
-        const int chunk = (rows + rgb - 1) / rgb;
-        const int slot = tid % bcols, g = tid / bcols;
-        if (g < rgb) {
-          const int c = j + 1 + slot;
-          const double w = part[c - 1];
-          const T coef = (T)(tau_s[j] * w);
-          const T* u = S + j * ld;
-          T* cc = S + c * ld;
-          int i = j + g * chunk;
-          const int i1 = min(i + chunk, hl);
-          double ssq = 0.0;
-          if (i == j && i < i1) {
-            cc[j] -= coef;
-            ++i;
-          }
-          if (slot == 0) {
-            for (; i < i1; ++i) {
-              const T x = cc[i] - coef * u[i];
-              cc[i] = x;
-              if (i > j + 1) ssq = fma((double)x, (double)x, ssq);
-            }
-            nrm_part[g] = ssq;
-          } else {
-            for (; i < i1; ++i) cc[i] -= coef * u[i];
-          }
+      // Phase B: a_c -= tau_j w_c u_j; squared norm of column j+1's new tail.
+      if (g < rg) {
+        double w = 0.0;
+        for (int gg = 0; gg < rg; ++gg) w += part[gg * acols + slot];
+        const T coef = (T)(tau_s[j] * w);
+        T* cc = S + c * ld;
+        int i = i0;
+        if (i == j && i < i1) {
+          cc[j] -= coef;
+          ++i;
         }
-        if (tid == 0) sh_nrg = rgb;
+        if (slot == 0) {
+          double ssq = 0.0;
+          for (; i < i1; ++i) {
+            const T x = cc[i] - coef * colj[i];
+            cc[i] = x;
+            if (i > j + 1) ssq = fma((double)x, (double)x, ssq);
+          }
+          nrm_part[g] = ssq;
+        } else {
+          for (; i < i1; ++i) cc[i] -= coef * colj[i];
+        }
       }
+      if (tid == 0) sh_nrg = rg;
       __syncthreads();
     }
+    __syncthreads();
 
+    // Z = strictly-upper(Y^T Y) in registers: 2x2 tiles (P, Q) with P <= Q
+    // over the upper triangle of n/2 x n/2 tile blocks, tile t = tid + k*NT.
+    const int nb = (n + 1) / 2;
+    const int ntiles = nb * (nb + 1) / 2;
+    constexpr int kMaxTiles = (NMAX / 2) * (NMAX / 2 + 1) / 2 / NT + 1;
+    double zacc[kMaxTiles][4];
+    auto yv = [&](int i, int col) -> double {
+      if (col >= n || i < col) return 0.0;
+      return i == col ? 1.0 : (double)S[col * ld + i];
+    };
+#pragma unroll
+    for (int k = 0; k < kMaxTiles; ++k) {
+      zacc[k][0] = zacc[k][1] = zacc[k][2] = zacc[k][3] = 0.0;
+      const int t = tid + k * NT;
+      if (t < ntiles) {
+        // t -> (P, Q) with P <= Q, ordered by Q so that the lanes of a warp
+        // loop over nearly the same rows [2Q, hl).
+        int Q = 0;
+        while ((Q + 1) * (Q + 2) / 2 <= t) ++Q;
+        const int P = t - Q * (Q + 1) / 2;
+        const int p0 = 2 * P, q0 = 2 * Q;
+        double z00 = 0, z01 = 0, z10 = 0, z11 = 0;
+        for (int i = q0; i < hl; ++i) {
+          const double a0 = yv(i, p0), a1 = yv(i, p0 + 1);
+          const double b0 = yv(i, q0), b1 = yv(i, q0 + 1);
+          z00 = fma(a0, b0, z00);
+          z01 = fma(a0, b1, z01);
+          z10 = fma(a1, b0, z10);
+          z11 = fma(a1, b1, z11);
+        }
+        zacc[k][0] = z00;
+        zacc[k][1] = z01;
+        zacc[k][2] = z10;
+        zacc[k][3] = z11;
+      }
+    }
     // Write back Y (below the diagonal) and R_i (on and above) in place, the
     // leaf R factor to the tree's level-0 items, and tau.
-    for (int c = 0; c < n; ++c) {
-      T* dst = Ag + (int64_t)c * a.lda;
-      for (int i = tid; i < hl; i += NT) dst[i] = S[c * ld + i];
+    for (int cc = 0; cc < n; ++cc) {
+      T* dst = Ag + (int64_t)cc * a.lda;
+      for (int i = tid; i < hl; i += NT) dst[i] = S[cc * ld + i];
     }
     T* Rl = a.R + leaf * (int64_t)n * n;
     for (int idx = tid; idx < n * n; idx += NT) {
-      const int i = idx % n, c = idx / n;
-      Rl[idx] = i <= c ? S[c * ld + i] : T(0);
+      const int i = idx % n, cc = idx / n;
+      Rl[idx] = i <= cc ? S[cc * ld + i] : T(0);
     }
-    for (int c = tid; c < n; c += NT) a.tau[leaf * (int64_t)n + c] = (T)tau_s[c];
+    for (int cc = tid; cc < n; cc += NT) a.tau[leaf * (int64_t)n + cc] = (T)tau_s[cc];
     __syncthreads();
-    // Compact-WY T from the z values stored in the T buffer.
-    T* Tg = a.Tw + leaf * (int64_t)n * n;
+    // Tm = Z above the diagonal, tau on it, zero below.
     for (int idx = tid; idx < n * n; idx += NT) {
-      const int p = idx % n, jj = idx / n;
-      Tm[idx] = p < jj ? (double)Tg[idx] : 0.0;
+      const int p = idx % n, q = idx / n;
+      Tm[idx] = p == q ? tau_s[p] : 0.0;
     }
     __syncthreads();
-    build_t(Tm, tau_s, n);
+#pragma unroll
+    for (int k = 0; k < kMaxTiles; ++k) {
+      const int t = tid + k * NT;
+      if (t < ntiles) {
+        int Q = 0;
+        while ((Q + 1) * (Q + 2) / 2 <= t) ++Q;
+        const int P = t - Q * (Q + 1) / 2;
+        const int p0 = 2 * P, q0 = 2 * Q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int p = p0 + (e >> 1), q = q0 + (e & 1);
+          if (p < q && q < n) Tm[p + q * n] = zacc[k][e];
+        }
+      }
+    }
+    __syncthreads();
+    build_t_doubling(Tm, Wt, n);
+    T* Tg = a.Tw + leaf * (int64_t)n * n;
     for (int idx = tid; idx < n * n; idx += NT) Tg[idx] = (T)Tm[idx];
     __syncthreads();
   }
@@ -193,28 +239,26 @@ int leaf_factor_ld(int hmax) { return hmax | 1; }
 
 size_t leaf_factor_smem(int n, int hmax, size_t elem) {
   const int ld = leaf_factor_ld(hmax);
-  size_t tile = align_up(elem * (size_t)n * ld, 16);
-  const size_t tm = align_up(sizeof(double) * (size_t)n * n, 16);
-  if (tm > tile) tile = tm;
-  return tile + sizeof(double) * (2 * kLeafThreads + (size_t)n);
+  const int nt = elem == 8 ? kLeafThreads64 : kLeafThreads32;
+  return tile_region(n, ld, elem) + sizeof(double) * (2 * (size_t)nt + (size_t)n);
 }
 
 template <typename T>
 cudaError_t launch_leaf_factor(const LeafFactorArgs<T>& a, cudaStream_t s) {
   if (a.nleaves <= 0 || a.n <= 0) return cudaSuccess;
-  const int hmax = a.ld_s;
-  const size_t smem = leaf_factor_smem(a.n, hmax, sizeof(T));
-  auto kern = leaf_factor_kernel<T, kLeafThreads>;
+  constexpr int NT = sizeof(T) == 8 ? kLeafThreads64 : kLeafThreads32;
+  const size_t smem = leaf_factor_smem(a.n, a.ld_s, sizeof(T));
+  auto kern = a.n <= 64 ? leaf_factor_kernel<T, NT, 64> : leaf_factor_kernel<T, NT, kMaxN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLeafThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > a.nleaves) grid = a.nleaves;
-  kern<<<(unsigned)grid, kLeafThreads, smem, s>>>(a);
+  kern<<<(unsigned)grid, NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

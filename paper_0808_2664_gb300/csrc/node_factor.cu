@@ -28,7 +28,7 @@ __host__ __device__ inline int node_ld(int n) { return n | 1; }
 
 __host__ __device__ inline size_t node_tile_bytes(int n, int q, size_t elem) {
   size_t tile = align_up_n(elem * (size_t)q * n * node_ld(n), 16);
-  const size_t tm = align_up_n(sizeof(double) * (size_t)n * n, 16);
+  const size_t tm = align_up_n(sizeof(double) * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
   return tile > tm ? tile : tm;
 }
 
@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(NT) node_factor_kernel(NodeFactorArgs<T> a) {
   double* nrm_part = part + NT;
   double* tau_s = nrm_part + NT;
   double* Tm = reinterpret_cast<double*>(smem);
+  double* Wt = Tm + (size_t)n * n;
   __shared__ double sh_scale;
   __shared__ int sh_nrg;
   const int tid = threadIdx.x;
@@ -208,10 +209,10 @@ __global__ void __launch_bounds__(NT) node_factor_kernel(NodeFactorArgs<T> a) {
     __syncthreads();
     for (int64_t idx = tid; idx < nn; idx += NT) {
       const int p = (int)(idx % n), jj = (int)(idx / n);
-      Tm[idx] = p < jj ? (double)To[idx] : 0.0;
+      Tm[idx] = p < jj ? (double)To[idx] : (p == jj ? tau_s[p] : 0.0);
     }
     __syncthreads();
-    build_t(Tm, tau_s, n);
+    build_t_doubling(Tm, Wt, n);
     for (int64_t idx = tid; idx < nn; idx += NT) To[idx] = (T)Tm[idx];
     __syncthreads();
   }

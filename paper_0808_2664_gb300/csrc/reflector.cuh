@@ -77,27 +77,39 @@ __device__ __forceinline__ double scaled_norm(int len, Get get) {
 
 __device__ __forceinline__ int pow2_floor(int x) { return x <= 1 ? 1 : 1 << (31 - __clz(x)); }
 
-// Build the compact-WY T (upper triangular, n x n, column-major ld n, in
-// FP64 shared memory) from tau and the strictly upper part of Y^T Y, which
-// the caller has stored in Tm(p, j) for p < j.  Forward recurrence of
-// Schreiber and Van Loan (cited in Section 2.1):
-//   T(j, j) = tau_j,   T(0:j, j) = -tau_j T(0:j, 0:j) (Y(:, 0:j)^T y_j).
-// Every thread of the block calls this.
-__device__ __forceinline__ void build_t(double* Tm, const double* tau, int n) {
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int p = idx % n, j = idx / n;
-    if (p == j) Tm[idx] = tau[j];
-    else if (p > j) Tm[idx] = 0.0;
-  }
-  __syncthreads();
-  for (int j = 1; j < n; ++j) {
-    double s = 0.0;
-    const int p = threadIdx.x;
-    if (p < j) {
-      for (int q = p; q < j; ++q) s = fma(Tm[p + q * n], Tm[q + j * n], s);
+// Build the compact-WY T (upper triangular, n x n, column-major ld n, FP64
+// shared memory) in place.  On entry Tm holds tau on the diagonal, the
+// strictly upper part of Y^T Y above it (Tm(p, q) = y_p^T y_q) and zeros
+// below.  Schreiber and Van Loan (cited in Section 2.1) give, for two blocks
+// of reflectors, I - Y T Y^T with T = [T1, -T1 (Y1^T Y2) T2; 0, T2]; applying
+// that merge to aligned blocks of 1, 2, 4, ... columns builds T in log2(n)
+// levels of independent triangular products.  Wt needs n*n/2 doubles.  Every
+// thread of the block calls this.
+__device__ __forceinline__ void build_t_doubling(double* Tm, double* Wt, int n) {
+  for (int b = 1; b < n; b *= 2) {
+    const int npairs = (n + 2 * b - 1) / (2 * b);
+    const int bb = b * b;
+    // Pass 1: W = Z12 T2 for every pair, W(p - s, q - s - b) stored at Wt + pair * b * b.
+    for (int idx = threadIdx.x; idx < npairs * bb; idx += blockDim.x) {
+      const int pair = idx / bb, rem = idx % bb;
+      const int pl = rem % b, ql = rem / b;
+      const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
+      if (q >= n) continue;
+      double acc = 0.0;
+      for (int r = s + b; r <= q; ++r) acc = fma(Tm[p + r * n], Tm[r + q * n], acc);
+      Wt[pair * bb + pl + ql * b] = acc;
     }
     __syncthreads();
-    if (p < j) Tm[p + j * n] = -tau[j] * s;
+    // Pass 2: T12 = -T1 W.
+    for (int idx = threadIdx.x; idx < npairs * bb; idx += blockDim.x) {
+      const int pair = idx / bb, rem = idx % bb;
+      const int pl = rem % b, ql = rem / b;
+      const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
+      if (q >= n) continue;
+      double acc = 0.0;
+      for (int r = p; r < s + b; ++r) acc = fma(Tm[p + r * n], Wt[pair * bb + (r - s) + ql * b], acc);
+      Tm[p + q * n] = -acc;
+    }
     __syncthreads();
   }
 }

@@ -12,7 +12,8 @@ constexpr int kStatusNonfinite = 1;
 constexpr int kStatusTimeout = 2;
 
 // Threads per CTA of the factor and apply kernels.
-constexpr int kLeafThreads = 256;
+constexpr int kLeafThreads64 = 128;  // FP64 leaves
+constexpr int kLeafThreads32 = 256;  // FP32-storage leaves
 constexpr int kNodeThreads = 128;
 constexpr int kApplyThreads = 256;
 // Columns of C handled by one CTA of the apply kernels.
