@@ -54,7 +54,8 @@ enum tsqr_status_code {
   TSQR_ERR_TIMEOUT = 3,     /* a device-side bounded wait gave up */
   TSQR_ERR_NONFINITE = 4,   /* NaN or Inf met in a column norm or pivot */
   TSQR_ERR_UNSUPPORTED = 5, /* shape / precision combination not supported */
-  TSQR_ERR_HANDLE = 6       /* NULL, destroyed or mismatched handle */
+  TSQR_ERR_HANDLE = 6,      /* NULL, destroyed or mismatched handle */
+  TSQR_ERR_TOO_LARGE = 7    /* problem exceeds tsqr_factor_r_noalloc's static scratch */
 };
 
 enum tsqr_precision {
@@ -136,6 +137,27 @@ int tsqr_q_info(tsqr_q_t q, int64_t* m, int64_t* n, int32_t* precision, int64_t*
 
 /* tsqr_q_destroy: frees the handle and its workspace (after its queued work). */
 int tsqr_q_destroy(tsqr_q_t q);
+
+/*
+ * tsqr_factor_r_noalloc: R (n x n, diag(R) >= 0, zeros below the diagonal)
+ * of the FP64 m x n matrix A, allocating no device memory.  The paper has no
+ * counterpart; this exists for callers that cannot call cudaMalloc -- code
+ * running inside another allocator's callback, plugins of frameworks that
+ * own all device memory, processes whose memory budget is fixed up front.
+ *   Arguments as for tsqr_factor (A is overwritten by the leaf reflectors),
+ *   without options or a Q handle: default leaf height, binary tree.
+ *   Workspace comes from one static 64 MiB device array inside the library,
+ *   held by every GPU that loads the library until the process exits.
+ *   Problems whose tree workspace does not fit (about n*n*8 bytes * 5 per
+ *   leaf; at n = 64 with 128-row leaves, m up to roughly 50,000 rows) return
+ *   TSQR_ERR_TOO_LARGE without touching the GPU.
+ *   The first call on a device looks up the array's address (make it before
+ *   any stream capture).  Calls share the array: calls whose GPU work
+ *   overlaps (other streams, other host threads) race and must be
+ *   serialised by the caller.  Device-side conditions are not reported.
+ */
+int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t lda, double* R, int64_t ldr,
+                          tsqr_stream_t stream);
 
 /* ---------------------------------------------------------------- CAQR -- */
 

@@ -35,6 +35,7 @@ SIGNATURES = {
     "tsqr_sync_status": ([vp, vp], ctypes.c_int),
     "tsqr_q_info": ([vp, pi64, pi64, pi32, pi64, pi64, pi32, pi32], ctypes.c_int),
     "tsqr_q_destroy": ([vp], ctypes.c_int),
+    "tsqr_factor_r_noalloc": ([i64, i64, vp, i64, vp, i64, vp], ctypes.c_int),
     "caqr_factor": ([i64, i64, vp, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
     "caqr_apply_qt": ([vp, i64, vp, i64, vp], ctypes.c_int),
     "caqr_apply_q": ([vp, i64, vp, i64, vp], ctypes.c_int),

@@ -671,6 +671,7 @@ const char* tsqr_status_string(int code) {
     case TSQR_ERR_NONFINITE: return "non-finite value in a column norm or pivot";
     case TSQR_ERR_UNSUPPORTED: return "unsupported shape or precision";
     case TSQR_ERR_HANDLE: return "invalid handle";
+    case TSQR_ERR_TOO_LARGE: return "problem exceeds the no-allocation entry point's static scratch";
     default: return "unknown status";
   }
 }
