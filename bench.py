@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--caqr-n", type=int, default=8192, help="square CAQR size for the CAQR variant")
+    p.add_argument("--caqr-b", type=int, default=64)
     return p.parse_args()
 
 
@@ -201,6 +203,50 @@ def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False):
             "q": q, "A0": A0, "A": A, "Q": Q, "R": R}
 
 
+def caqr_run(tq, torch, args, steps, warmup):
+    """Square FP64 CAQR, U[-1, 1] entries, panel width b: GFLOP/s of 4n^3/3 and the update's roofline."""
+    n, b = args.caqr_n, args.caqr_b
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(3001)
+    A0 = (torch.rand((n, n), generator=g, dtype=torch.float64, device=dev) * 2 - 1).t()
+    A = tq.colmajor(n, n, torch.float64, dev)
+    q = tq.caqr_q_create(n, n, b, torch.float64, dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        A.copy_(A0)
+        q.refactor(A)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    q.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st = q.stage_times()
+    q.set_timing(False)
+    Q = q.form_q()
+    R = torch.triu(A)
+    berr = (torch.linalg.norm(A0 - Q @ R) / torch.linalg.norm(A0)).item()
+    orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.t() @ Q).item()
+    flops = 4.0 * n ** 3 / 3.0
+    upd_ms = st["leaf_apply"][0] / steps
+    upd_flops = sum(4.0 * (n - j) * b * (n - j - b) for j in range(0, n, b))
+    return {"value": flops / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "n": n, "b": b,
+            "update_precision": "fp64", "backward_error": berr, "orthogonality": orth,
+            "tolerance": 10 * n * 2.0 ** -52 * n ** 0.5, "status": q.sync_status(),
+            "update_roofline": {"bound": "alu", "kernel": "leaf_apply_kernel<double> (trailing update)",
+                                "achieved": upd_flops / (upd_ms / 1e3) / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
+                                "unit": "TFLOP/s", "frac": upd_flops / (upd_ms / 1e3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3)},
+            "stage_ms_per_step": {k: v[0] / steps for k, v in st.items()}}
+
+
 def e2e_run(tq, torch, args, q, steps, warmup):
     """Public API with host buffers: H2D of A, factor, form Q, D2H of Q and R each step."""
     m, n = args.m, args.n
@@ -304,6 +350,9 @@ def ours(args, world, rank, local):
             "value": world * m / (v["ms_total"] / max(3, args.steps) / 1e3), "unit": "rows/s",
             "ms_per_step": v["ms_total"] / max(3, args.steps), "backward_error": v["berr"],
             "orthogonality": v["orth"], "status": v["status"]}
+        del v
+        torch.cuda.empty_cache()
+        variants["caqr_fp64"] = caqr_run(tq, torch, args, steps=3, warmup=3)
 
     if rank == 0:
         line = {

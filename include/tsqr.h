@@ -175,6 +175,16 @@ int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t lda, double* 
 int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
                 const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream);
 
+/*
+ * Plan-once form of CAQR: caqr_q_create plans every panel of an m x n
+ * problem with panel width b and allocates all panel workspaces at once;
+ * caqr_refactor then factors a matrix of that shape (device, lda >= m) in
+ * place with no allocation.  caqr_factor = create + refactor.
+ */
+int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, const tsqr_opts_t* opts,
+                  caqr_q_t* q, tsqr_stream_t stream);
+int caqr_refactor(caqr_q_t q, double* A, int64_t lda, tsqr_stream_t stream);
+
 /* caqr_apply_qt: C (m x k, ldc >= m) <- Q^T C, panels in factorisation order. */
 int caqr_apply_qt(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream);
 
@@ -185,6 +195,11 @@ int caqr_apply_q(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stre
 int caqr_form_q(caqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream);
 
 int caqr_sync_status(caqr_q_t q, tsqr_stream_t stream);
+
+/* Stage timing summed over every panel of a CAQR handle; the leaf-apply
+ * stage is the trailing-matrix update (same semantics as the tsqr_ forms). */
+int caqr_q_set_timing(caqr_q_t q, int32_t enable);
+int caqr_q_stage_times(caqr_q_t q, double* ms, int64_t* launches, int32_t count);
 int caqr_q_destroy(caqr_q_t q);
 
 /* ----------------------------------------------------------- tracing -- */

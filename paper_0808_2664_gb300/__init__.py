@@ -17,7 +17,7 @@ from ._lib import TsqrError, TsqrOpts, check, lib
 
 __all__ = [
     "TsqrError", "QTree", "CaqrQ", "colmajor", "as_colmajor", "tsqr_factor", "tsqr_q_create",
-    "caqr_factor", "PREC_FP64", "PREC_FP32",
+    "caqr_factor", "caqr_q_create", "PREC_FP64", "PREC_FP32",
 ]
 
 PREC_FP64 = 0
@@ -224,6 +224,23 @@ class CaqrQ:
         check(lib().caqr_form_q(self.ptr, ctypes.c_void_p(Q.data_ptr()), _ld(Q, "Q"), _stream(Q)), "caqr_form_q")
         return Q
 
+    def set_timing(self, enable: bool = True) -> None:
+        check(lib().caqr_q_set_timing(self.ptr, 1 if enable else 0), "caqr_q_set_timing")
+
+    def stage_times(self) -> dict:
+        ms = (ctypes.c_double * 4)()
+        nl = (ctypes.c_int64 * 4)()
+        check(lib().caqr_q_stage_times(self.ptr, ms, nl, 4), "caqr_q_stage_times")
+        return {name: (ms[i], nl[i]) for i, name in enumerate(QTree.STAGES)}
+
+    def refactor(self, A):
+        """Factor a new m x n matrix in place with the planned workspace (no allocation)."""
+        if tuple(A.shape) != (self.m, self.n) or A.dtype != self.dtype:
+            raise ValueError("A does not match the handle's shape / dtype")
+        check(lib().caqr_refactor(self.ptr, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), _stream(A)), "caqr_refactor")
+        self.A = A
+        return A
+
     def sync_status(self) -> int:
         torch = _torch()
         return lib().caqr_sync_status(self.ptr, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
@@ -238,6 +255,18 @@ class CaqrQ:
             self.destroy()
         except Exception:
             pass
+
+
+def caqr_q_create(m: int, n: int, b: int = 64, dtype=None, device="cuda", update_precision: int = PREC_FP64,
+                  leaf_rows: int = 0, arity: int = 0) -> CaqrQ:
+    """Plan and allocate a CAQR handle; factor with CaqrQ.refactor."""
+    torch = _torch()
+    dtype = dtype or torch.float64
+    h = ctypes.c_void_p()
+    o = _opts(leaf_rows, arity)
+    check(lib().caqr_q_create(m, n, b, update_precision, ctypes.byref(o), ctypes.byref(h),
+                              ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)), "caqr_q_create")
+    return CaqrQ(h, m, n, dtype, None)
 
 
 def caqr_factor(A, b: int = 64, update_precision: int = PREC_FP64, leaf_rows: int = 0, arity: int = 0,

@@ -37,11 +37,15 @@ SIGNATURES = {
     "tsqr_q_destroy": ([vp], ctypes.c_int),
     "tsqr_factor_r_noalloc": ([i64, i64, vp, i64, vp, i64, vp], ctypes.c_int),
     "caqr_factor": ([i64, i64, vp, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
+    "caqr_q_create": ([i64, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
+    "caqr_refactor": ([vp, vp, i64, vp], ctypes.c_int),
     "caqr_apply_qt": ([vp, i64, vp, i64, vp], ctypes.c_int),
     "caqr_apply_q": ([vp, i64, vp, i64, vp], ctypes.c_int),
     "caqr_form_q": ([vp, vp, i64, vp], ctypes.c_int),
     "caqr_sync_status": ([vp, vp], ctypes.c_int),
     "caqr_q_destroy": ([vp], ctypes.c_int),
+    "caqr_q_set_timing": ([vp, i32], ctypes.c_int),
+    "caqr_q_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), pi64, i32], ctypes.c_int),
     "tsqr_q_set_timing": ([vp, i32], ctypes.c_int),
     "tsqr_q_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), pi64, i32], ctypes.c_int),
     "tsqr_status_string": ([ctypes.c_int], ctypes.c_char_p),

@@ -522,24 +522,20 @@ int tsqr_q_stage_times(tsqr_q_t q, double* ms, int64_t* launches, int32_t count)
 
 // ------------------------------------------------------------------ CAQR --
 
-int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
-                const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
+int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, const tsqr_opts_t* opts, caqr_q_t* q,
+                  tsqr_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (q) *q = nullptr;
-  if (m < 0) return -1;
-  if (n < 0 || n > m) return -2;
-  if (m > 0 && n > 0 && !A) return -3;
-  if (lda < (m > 1 ? m : 1)) return -4;
-  if (b < 1) return -5;
-  if (update_precision != TSQR_PREC_FP64) return -6;
-  if (m == 0 || n == 0) return TSQR_OK;
+  if (!q) return -6;
+  *q = nullptr;
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (b < 1) return -3;
+  if (update_precision != TSQR_PREC_FP64) return -4;
   caqr_q_s* c = new (std::nothrow) caqr_q_s();
   if (!c) return TSQR_ERR_NOMEM;
   c->m = m;
   c->n = n;
   c->b = b;
-  c->A = A;
-  c->lda = lda;
   // Plan every panel, then one allocation for all of their workspaces.
   std::vector<tsqr_q_s*> plans;
   size_t total = 0;
@@ -552,7 +548,7 @@ int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t
       break;
     }
     rc = make_plan(p, m - j0, jb, TSQR_PREC_FP64, opts);
-    if (rc == -4) rc = -7;
+    if (rc == -4) rc = -5;
     plans.push_back(p);
     total += workspace_bytes(p);
   }
@@ -576,15 +572,52 @@ int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t
     cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
     if (e != cudaSuccess) rc = cuda_err(e);
   }
-  // Right-looking loop: TSQR of panel j, then (Q_j D_j)^T on the trailing columns.
-  for (size_t j = 0; j < c->panels.size() && rc == TSQR_OK; ++j) {
-    tsqr_q_s* p = c->panels[j];
-    const int64_t j0 = (int64_t)j * b;
-    double* P = A + j0 + j0 * lda;
-    rc = refactor(p, P, lda, P, lda, false, s);
-    const int64_t kt = n - j0 - p->n;
-    if (rc == TSQR_OK && kt > 0) rc = apply_common(p, kApplyQT, kt, A + j0 + (j0 + p->n) * lda, lda, s);
+  if (rc != TSQR_OK) {
+    caqr_q_destroy(c);
+    return rc;
   }
+  *q = c;
+  return TSQR_OK;
+}
+
+int caqr_refactor(caqr_q_t c, double* A, int64_t lda, tsqr_stream_t stream) {
+  if (!valid(c)) return TSQR_ERR_HANDLE;
+  if (!A) return -2;
+  if (lda < c->m) return -3;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->A = A;
+  c->lda = lda;
+  // Right-looking loop: TSQR of panel j, then (Q_j D_j)^T on the trailing columns.
+  for (size_t j = 0; j < c->panels.size(); ++j) {
+    tsqr_q_s* p = c->panels[j];
+    const int64_t j0 = (int64_t)j * c->b;
+    double* P = A + j0 + j0 * lda;
+    int rc = refactor(p, P, lda, P, lda, false, s);
+    if (rc != TSQR_OK) return rc;
+    const int64_t kt = c->n - j0 - p->n;
+    if (kt > 0) {
+      rc = apply_common(p, kApplyQT, kt, A + j0 + (j0 + p->n) * lda, lda, s);
+      if (rc != TSQR_OK) return rc;
+    }
+  }
+  return TSQR_OK;
+}
+
+int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
+                const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (q) *q = nullptr;
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (m > 0 && n > 0 && !A) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (b < 1) return -5;
+  if (update_precision != TSQR_PREC_FP64) return -6;
+  if (m == 0 || n == 0) return TSQR_OK;
+  caqr_q_t c = nullptr;
+  int rc = caqr_q_create(m, n, b, update_precision, opts, &c, stream);
+  if (rc != TSQR_OK) return rc == -5 ? -7 : rc;
+  rc = caqr_refactor(c, A, lda, stream);
   if (rc != TSQR_OK || !q) {
     cudaStreamSynchronize(s);
     caqr_q_destroy(c);
@@ -638,6 +671,34 @@ int caqr_form_q(caqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream) {
     const int64_t j0 = (int64_t)j * q->b;
     int rc = apply_common(q->panels[j], kApplyQ, q->n - j0, (double*)Q + j0 + j0 * ldq, ldq, s);
     if (rc != TSQR_OK) return rc;
+  }
+  return TSQR_OK;
+}
+
+int caqr_q_set_timing(caqr_q_t q, int32_t enable) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  for (auto* p : q->panels) tsqr_q_set_timing(p, enable);
+  return TSQR_OK;
+}
+
+int caqr_q_stage_times(caqr_q_t q, double* ms, int64_t* launches, int32_t count) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (count < 0 || count > TSQR_NUM_STAGES) return -4;
+  double tot_ms[TSQR_NUM_STAGES] = {0, 0, 0, 0};
+  int64_t tot_l[TSQR_NUM_STAGES] = {0, 0, 0, 0};
+  for (auto* p : q->panels) {
+    double pm[TSQR_NUM_STAGES];
+    int64_t pl[TSQR_NUM_STAGES];
+    int rc = tsqr_q_stage_times(p, pm, pl, TSQR_NUM_STAGES);
+    if (rc != TSQR_OK) return rc;
+    for (int st = 0; st < TSQR_NUM_STAGES; ++st) {
+      tot_ms[st] += pm[st];
+      tot_l[st] += pl[st];
+    }
+  }
+  for (int st = 0; st < count; ++st) {
+    if (ms) ms[st] = tot_ms[st];
+    if (launches) launches[st] = tot_l[st];
   }
   return TSQR_OK;
 }

@@ -1,0 +1,82 @@
+"""Parity of the CUDA CAQR path (TSQR panels + trailing updates) with the CPU oracle.
+
+CAQR returns the same factorisation as unblocked Householder QR once diag(R)
+is made non-negative, so R and the thin Q are compared with the oracle's, and
+Q^T C's top n rows with the oracle's thin-Q product.  Tolerance: the FP64
+bound 10 * n * eps * sqrt(m), times the condition number for R and Q.
+"""
+import numpy as np
+import pytest
+
+from conftest import fp64_tol
+from paper_0808_2664_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_0808_2664_gb300 as tq  # noqa: E402
+
+
+def dev(A):
+    return tq.as_colmajor(torch.from_numpy(np.asfortranarray(A)).to("cuda"))
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,b,h", [
+    (256, 256, 32, 0),     # square, several panels
+    (512, 512, 64, 128),   # square, panel width 64
+    (1000, 200, 48, 0),    # tall, ragged last panel
+    (3000, 128, 64, 0),    # tall n = 128 in FP64 via two 64-column panels
+    (300, 300, 7, 64),     # odd panel width
+    (120, 120, 120, 0),    # one panel: CAQR reduces to TSQR
+])
+def test_caqr_matches_oracle(oracle_mod, m, n, b, h):
+    A = inputs.uniform(m, n, seed=3000 + m + n)
+    Qo, Ro = oracle_mod.qr(A)
+    kappa = np.linalg.cond(A)
+    Ad = dev(A)
+    q = tq.caqr_factor(Ad, b=b, leaf_rows=h)
+    Q = q.form_q()
+    assert q.sync_status() == 0
+    R = np.triu(host(Ad)[:n, :n])
+    Qh = host(Q)
+    tol = fp64_tol(m, n)
+    assert np.all(np.diag(R) >= 0)
+    assert np.linalg.norm(R - Ro) / np.linalg.norm(Ro) <= tol * kappa
+    assert np.linalg.norm(Qh - Qo) <= tol * kappa * np.sqrt(n)
+    assert np.linalg.norm(A - Qh @ R) / np.linalg.norm(A) <= tol
+    assert np.linalg.norm(np.eye(n) - Qh.T @ Qh) <= tol
+    # Q^T C: top n rows are unique; Q (Q^T C) = C.
+    C = inputs.gaussian(m, 19, seed=5)
+    Cd = dev(C)
+    q.apply_qt(Cd)
+    assert np.linalg.norm(host(Cd)[:n] - Qo.T @ C) <= 4 * tol * kappa * np.linalg.norm(C)
+    q.apply_q(Cd)
+    assert np.linalg.norm(host(Cd) - C) <= 4 * tol * np.linalg.norm(C)
+
+
+def test_caqr_ill_conditioned_backward_stable():
+    m = n = 384
+    A = inputs.ill_conditioned(m, n, 31, cond=1e12)
+    Ad = dev(A)
+    q = tq.caqr_factor(Ad, b=64)
+    Q = host(q.form_q())
+    R = np.triu(host(Ad)[:n, :n])
+    assert np.linalg.norm(A - Q @ R) / np.linalg.norm(A) <= fp64_tol(m, n)
+    assert np.linalg.norm(np.eye(n) - Q.T @ Q) <= fp64_tol(m, n)
+
+
+def test_caqr_argument_errors():
+    A = dev(inputs.uniform(64, 64, 1))
+    with pytest.raises(tq.TsqrError) as ei:
+        tq.caqr_factor(A, b=0)
+    assert ei.value.code == -5
+    with pytest.raises(tq.TsqrError) as ei:
+        tq.caqr_factor(A, b=16, update_precision=7)
+    assert ei.value.code == -6
