@@ -1,0 +1,86 @@
+// Throughput probes for the roofline denominators that are not in the
+// driver's measured peaks: FP64 FMA, FP32 FMA and FP64 mma.sync m8n8k4
+// (DMMA) rates, each from independent FMA chains over a full grid, timed with
+// CUDA events.  Build and run:
+//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o peak_probe peak_probe.cu && ./peak_probe
+#include <cstdio>
+#include <cuda_runtime.h>
+#define CK(x) do{cudaError_t e=(x); if(e!=cudaSuccess){printf("CUDA %s @%d\n",cudaGetErrorString(e),__LINE__); return 1;}}while(0)
+
+template<int CH>
+__global__ void fma64(double* out, int iters, double a, double b) {
+  double x[CH];
+  #pragma unroll
+  for (int c = 0; c < CH; ++c) x[c] = threadIdx.x * 1e-3 + c;
+  for (int i = 0; i < iters; ++i) {
+    #pragma unroll
+    for (int c = 0; c < CH; ++c) x[c] = fma(x[c], a, b);
+  }
+  double s = 0; 
+  #pragma unroll
+  for (int c = 0; c < CH; ++c) s += x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+template<int CH>
+__global__ void fma32(float* out, int iters, float a, float b) {
+  float x[CH];
+  #pragma unroll
+  for (int c = 0; c < CH; ++c) x[c] = threadIdx.x * 1e-3f + c;
+  for (int i = 0; i < iters; ++i) {
+    #pragma unroll
+    for (int c = 0; c < CH; ++c) x[c] = fmaf(x[c], a, b);
+  }
+  float s = 0;
+  #pragma unroll
+  for (int c = 0; c < CH; ++c) s += x[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+__global__ void dmma(double* out, int iters) {
+  double a = 1.0 + threadIdx.x * 1e-6, b = 0.5;
+  double c[4][2];
+  for (int k = 0; k < 4; ++k) { c[k][0] = 0; c[k][1] = 0; }
+  for (int i = 0; i < iters; ++i) {
+    #pragma unroll
+    for (int k = 0; k < 4; ++k)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                   : "+d"(c[k][0]), "+d"(c[k][1]) : "d"(a), "d"(b));
+  }
+  double s = 0; for (int k = 0; k < 4; ++k) s += c[k][0] + c[k][1];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+int main() {
+  int dev = 0; cudaDeviceProp p; CK(cudaGetDeviceProperties(&p, dev));
+  printf("name=%s sms=%d cc=%d.%d smem/block optin=%zu l2=%d\n", p.name, p.multiProcessorCount, p.major, p.minor,
+         p.sharedMemPerBlockOptin, p.l2CacheSize);
+  int sms = p.multiProcessorCount;
+  double* d; CK(cudaMalloc(&d, sizeof(double) * sms * 16 * 1024));
+  cudaEvent_t e0, e1; cudaEventCreate(&e0); cudaEventCreate(&e1);
+  for (int blocksPerSm : {1, 2, 4, 8}) {
+    for (int threads : {128, 256}) {
+      int grid = sms * blocksPerSm; int iters = 4096;
+      fma64<8><<<grid, threads>>>(d, 16, 1.0000001, 1e-9); CK(cudaDeviceSynchronize());
+      cudaEventRecord(e0); fma64<8><<<grid, threads>>>(d, iters, 1.0000001, 1e-9); cudaEventRecord(e1);
+      CK(cudaEventSynchronize(e1)); float ms; cudaEventElapsedTime(&ms, e0, e1);
+      double fl = 2.0 * 8 * iters * (double)grid * threads;
+      printf("fp64 fma: bps=%d thr=%d  %.3f ms  %.3f TFLOP/s\n", blocksPerSm, threads, ms, fl / ms / 1e9);
+    }
+  }
+  for (int blocksPerSm : {2, 4, 8}) {
+    int grid = sms * blocksPerSm, threads = 256, iters = 16384;
+    fma32<8><<<grid, threads>>>((float*)d, 16, 1.0000001f, 1e-9f); CK(cudaDeviceSynchronize());
+    cudaEventRecord(e0); fma32<8><<<grid, threads>>>((float*)d, iters, 1.0000001f, 1e-9f); cudaEventRecord(e1);
+    CK(cudaEventSynchronize(e1)); float ms; cudaEventElapsedTime(&ms, e0, e1);
+    double fl = 2.0 * 8 * iters * (double)grid * threads;
+    printf("fp32 fma: bps=%d  %.3f ms  %.3f TFLOP/s\n", blocksPerSm, ms, fl / ms / 1e9);
+  }
+  for (int blocksPerSm : {1, 2, 4}) {
+    int grid = sms * blocksPerSm, threads = 256, iters = 1024;
+    dmma<<<grid, threads>>>(d, 8); CK(cudaDeviceSynchronize());
+    cudaEventRecord(e0); dmma<<<grid, threads>>>(d, iters); cudaEventRecord(e1);
+    CK(cudaEventSynchronize(e1)); float ms; cudaEventElapsedTime(&ms, e0, e1);
+    double fl = 2.0 * 8 * 8 * 4 * 4.0 * iters * (double)grid * (threads / 32);
+    printf("dmma m8n8k4: bps=%d  %.3f ms  %.3f TFLOP/s\n", blocksPerSm, ms, fl / ms / 1e9);
+  }
+  CK(cudaFree(d));
+  return 0;
+}
