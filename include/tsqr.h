@@ -202,6 +202,51 @@ int caqr_q_set_timing(caqr_q_t q, int32_t enable);
 int caqr_q_stage_times(caqr_q_t q, double* ms, int64_t* launches, int32_t count);
 int caqr_q_destroy(caqr_q_t q);
 
+/* ------------------------------------------------------------- batched -- */
+
+/*
+ * Batched uneven TSQR: `count` independent problems A_i (m_i x n_i, m_i >=
+ * n_i, 1 <= n_i <= 64) factored by ONE persistent kernel launch.  Each
+ * problem gets its own leaves and tree (Section 2.1: every tree gives the same
+ * R); the launch walks a device work list of all leaves, then all tree levels,
+ * and a node starts when a device counter shows its children are done (a
+ * bounded wait; a wait that gives up latches TSQR_ERR_TIMEOUT).
+ */
+typedef struct tsqr_batch_s* tsqr_batch_t;
+
+typedef struct tsqr_batch_opts_s {
+  int32_t tile_kb;  /* leaf tile budget in KB: h = largest power of two with n*h*elem <= tile_kb KB (0 = auto) */
+  int32_t arity;    /* tree arity, 2..16 (0 = 2) */
+  int32_t autotune; /* nonzero: time (tile_kb, arity) candidates on scratch matrices of these shapes, keep the fastest */
+  int32_t reserved; /* must be 0 */
+} tsqr_batch_opts_t;
+
+/*
+ * tsqr_batch_create: plans the batch and binds it to the matrices.
+ *   m, n, lda, ldr : HOST arrays of count entries.
+ *   A, R           : HOST arrays of count DEVICE pointers (column-major A_i,
+ *                    overwritten like tsqr_factor's A; R_i receives n_i x n_i
+ *                    R with diag >= 0, zeros below).
+ *   precision      : TSQR_PREC_FP32 (FP32 storage, FP64 norms / tau) or FP64.
+ * Allocates all workspace and the device work list; the matrices must stay
+ * allocated while the handle lives.
+ */
+int tsqr_batch_create(int32_t count, const int64_t* m, const int64_t* n, void* const* A, const int64_t* lda,
+                      void* const* R, const int64_t* ldr, int32_t precision, const tsqr_batch_opts_t* opts,
+                      tsqr_batch_t* b, tsqr_stream_t stream);
+
+/* tsqr_batch_factor: factors every bound matrix (counter reset + one persistent kernel launch). */
+int tsqr_batch_factor(tsqr_batch_t b, tsqr_stream_t stream);
+
+/* tsqr_batch_factor_graph: the same launch sequence, captured once into a CUDA graph and replayed. */
+int tsqr_batch_factor_graph(tsqr_batch_t b, tsqr_stream_t stream);
+
+/* tsqr_batch_info: chosen tile budget and arity, number of work items, device bytes held. */
+int tsqr_batch_info(tsqr_batch_t b, int32_t* tile_kb, int32_t* arity, int64_t* items, int64_t* workspace_bytes);
+
+int tsqr_batch_sync_status(tsqr_batch_t b, tsqr_stream_t stream);
+int tsqr_batch_destroy(tsqr_batch_t b);
+
 /* ----------------------------------------------------------- tracing -- */
 
 /*

@@ -23,6 +23,11 @@ class TsqrOpts(ctypes.Structure):
     _fields_ = [("leaf_rows", ctypes.c_int64), ("arity", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
+class TsqrBatchOpts(ctypes.Structure):
+    _fields_ = [("tile_kb", ctypes.c_int32), ("arity", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 # name -> (argtypes, restype); mirrors include/tsqr.h.
 SIGNATURES = {
     "tsqr_factor": ([i64, i64, vp, i64, vp, i64, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
@@ -46,6 +51,13 @@ SIGNATURES = {
     "caqr_q_destroy": ([vp], ctypes.c_int),
     "caqr_q_set_timing": ([vp, i32], ctypes.c_int),
     "caqr_q_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), pi64, i32], ctypes.c_int),
+    "tsqr_batch_create": ([i32, pi64, pi64, ctypes.POINTER(vp), pi64, ctypes.POINTER(vp), pi64, i32,
+                           ctypes.POINTER(TsqrBatchOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
+    "tsqr_batch_factor": ([vp, vp], ctypes.c_int),
+    "tsqr_batch_factor_graph": ([vp, vp], ctypes.c_int),
+    "tsqr_batch_info": ([vp, pi32, pi32, pi64, pi64], ctypes.c_int),
+    "tsqr_batch_sync_status": ([vp, vp], ctypes.c_int),
+    "tsqr_batch_destroy": ([vp], ctypes.c_int),
     "tsqr_q_set_timing": ([vp, i32], ctypes.c_int),
     "tsqr_q_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), pi64, i32], ctypes.c_int),
     "tsqr_status_string": ([ctypes.c_int], ctypes.c_char_p),
