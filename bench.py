@@ -319,6 +319,48 @@ def batched_run(tq, torch, args, steps, warmup, count=2048):
     return res
 
 
+def grad_run(tq, torch, dtype, steps, warmup, m=1 << 20, n=128):
+    """Differentiable TSQR forward + backward at m x n (dQ, dR iid N(0, 1))."""
+    from paper_0808_2664_gb300 import autograd as tqa
+    from paper_0808_2664_gb300 import inputs
+
+    A = inputs.gaussian_device(m, n, 5555, dtype=dtype).t()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5556)
+    dQ = torch.randn((n, m), generator=g, dtype=dtype, device="cuda").t()
+    dR = tq.as_colmajor(torch.triu(torch.randn((n, n), generator=g, dtype=dtype, device="cuda")))
+    res = {}
+    for recompute in (False, True):
+        def step():
+            Q, R = tqa.qr_forward(A)
+            if recompute:
+                del Q, R
+                Q, R = tqa.qr_forward(A)
+            return tqa.qr_backward(Q, R, dQ, dR)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            dA = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res["recompute" if recompute else "store"] = {"ms_per_step": ms,
+                                                      "torch_peak_bytes": torch.cuda.max_memory_allocated()}
+    # Gradient check against the device forward by central differences is in the tests; here the
+    # forward's backward error on the last step.
+    Q, R = tqa.qr_forward(A)
+    Q64, R64, A64 = Q.double(), R.double(), A.double()
+    berr = (torch.linalg.norm(A64 - Q64 @ R64) / torch.linalg.norm(A64)).item()
+    res.update({"m": m, "n": n, "dtype": str(dtype).replace("torch.", ""), "forward_backward_error": berr,
+                "flops_fwd_bwd": 4.0 * m * n * n + 6.0 * m * n * n})
+    return res
+
+
 def measured_hbm():
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -434,6 +476,9 @@ def ours(args, world, rank, local):
         variants["caqr_fp64"] = caqr_run(tq, torch, args, steps=3, warmup=3)
         torch.cuda.empty_cache()
         variants["batched_fp32_2048"] = batched_run(tq, torch, args, steps=5, warmup=3)
+        torch.cuda.empty_cache()
+        variants["grad_fp64_1Mx128"] = grad_run(tq, torch, torch.float64, steps=3, warmup=3)
+        variants["grad_fp32_1Mx128"] = grad_run(tq, torch, torch.float32, steps=3, warmup=3)
 
     if rank == 0:
         line = {

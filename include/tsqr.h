@@ -202,6 +202,28 @@ int caqr_q_set_timing(caqr_q_t q, int32_t enable);
 int caqr_q_stage_times(caqr_q_t q, double* ms, int64_t* launches, int32_t count);
 int caqr_q_destroy(caqr_q_t q);
 
+/* ------------------------------------------------------------ gradient -- */
+
+/*
+ * tsqr_qr_backward: the adjoint of the thin QR A = Q R (diag(R) > 0, full
+ * column rank) for a loss with gradients dQ (m x n) and dR (n x n, only its
+ * upper triangle is read).  The paper has no gradient; this is the standard
+ * adjoint
+ *     M = R dR^T - dQ^T Q,   dA = (dQ + Q copyltu(M)) R^{-T},
+ * copyltu(M) = tril(M) + tril(M, -1)^T, computed on the device as a
+ * tall-skinny reduction (dQ^T Q), an n x n step (M, R^{-1} by back
+ * substitution, copyltu(M) R^{-T}) and a row-parallel product
+ * dA = [dQ, Q] [R^{-T}; copyltu(M) R^{-T}].
+ *   precision: TSQR_PREC_FP64 (double) or TSQR_PREC_FP32 (float) for every
+ *   array; all arrays device, column-major; dA must not alias the inputs.
+ *   status: NULL, or a device int that receives TSQR_ERR_NONFINITE's bit
+ *   (value 1) when R has a zero or non-finite diagonal entry.
+ * Temporary device memory comes from cudaMallocAsync on `stream`.
+ */
+int tsqr_qr_backward(int64_t m, int64_t n, int32_t precision, const void* Q, int64_t ldq, const void* R, int64_t ldr,
+                     const void* dQ, int64_t lddq, const void* dR, int64_t lddr, void* dA, int64_t ldda, int* status,
+                     tsqr_stream_t stream);
+
 /* ------------------------------------------------------------- batched -- */
 
 /*

@@ -214,6 +214,7 @@ void oracle_qr_backward(int64_t m, int64_t n, const double* Q, const double* R, 
                         double* dA) {
   double* M = (double*)malloc(sizeof(double) * (size_t)(n * n > 0 ? n * n : 1));
   double* S = (double*)malloc(sizeof(double) * (size_t)(n * n > 0 ? n * n : 1));
+#pragma omp parallel for schedule(dynamic) if (m * n * n > 1000000)
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < n; ++i) {
       double a = 0.0; /* (R dR^T)_ij = sum_k R_ik dR_jk */

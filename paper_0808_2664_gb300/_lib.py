@@ -51,6 +51,7 @@ SIGNATURES = {
     "caqr_q_destroy": ([vp], ctypes.c_int),
     "caqr_q_set_timing": ([vp, i32], ctypes.c_int),
     "caqr_q_stage_times": ([vp, ctypes.POINTER(ctypes.c_double), pi64, i32], ctypes.c_int),
+    "tsqr_qr_backward": ([i64, i64, i32, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp], ctypes.c_int),
     "tsqr_batch_create": ([i32, pi64, pi64, ctypes.POINTER(vp), pi64, ctypes.POINTER(vp), pi64, i32,
                            ctypes.POINTER(TsqrBatchOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
     "tsqr_batch_factor": ([vp, vp], ctypes.c_int),
