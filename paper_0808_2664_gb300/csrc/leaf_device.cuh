@@ -13,17 +13,17 @@ constexpr int kLeafMinRows = 8;
 
 __host__ __device__ inline size_t leaf_align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Bytes of the region that holds the leaf tile and, after write-back, the
-// FP64 T matrix plus the doubling workspace.
+// Bytes of the region that holds the leaf tile and, after write-back, the T
+// matrix plus the doubling workspace (both in the storage type).
 __host__ __device__ inline size_t leaf_tile_region(int n, int ld, size_t elem) {
   const size_t tile = leaf_align_up(elem * (size_t)n * ld, 16);
-  const size_t tm = leaf_align_up(sizeof(double) * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
+  const size_t tm = leaf_align_up(elem * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
   return tile > tm ? tile : tm;
 }
 
 // Shared-memory bytes for a leaf of up to ld rows with NT threads.
 __host__ __device__ inline size_t leaf_smem_bytes(int n, int ld, size_t elem, int nt) {
-  return leaf_tile_region(n, ld, elem) + sizeof(double) * (2 * (size_t)nt + (size_t)n);
+  return leaf_tile_region(n, ld, elem) + (elem + sizeof(double)) * (size_t)nt + sizeof(double) * (size_t)n;
 }
 
 // Factors one leaf: rows Ag[0..hl) (column stride lda) of an n-column matrix,
@@ -34,12 +34,13 @@ template <typename T, int NT, int NMAX>
 __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl, T* taul, T* Tg, int* status,
                                 unsigned char* smem) {
   T* S = reinterpret_cast<T*>(smem);
-  double* part = reinterpret_cast<double*>(smem + leaf_tile_region(n, ld, sizeof(T)));  // NT partial dots
-  double* nrm_part = part + NT;                                                          // NT partial norms
-  double* tau_s = nrm_part + NT;                                                         // n
-  double* Tm = reinterpret_cast<double*>(smem);  // n x n, after write-back
-  double* Wt = Tm + (size_t)n * n;               // doubling workspace
-  __shared__ int sh_nrg;
+  // Products (dots, Y^T Y, T) run in the storage type T; squared norms and
+  // the reflector scalars run in FP64.
+  T* part = reinterpret_cast<T*>(smem + leaf_tile_region(n, ld, sizeof(T)));  // NT partial dots
+  double* nrm_part = reinterpret_cast<double*>(part + NT);                    // scratch (n coefficients)
+  double* tau_s = nrm_part + NT;                                              // n
+  T* Tm = reinterpret_cast<T*>(smem);  // n x n, after write-back
+  T* Wt = Tm + (size_t)n * n;          // doubling workspace
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   for (int c = 0; c < n; ++c) {
@@ -47,25 +48,19 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
     for (int i = tid; i < hl; i += NT) S[c * ld + i] = src[i];
   }
   __syncthreads();
-  {
-    double s = 0.0;
-    for (int i = 1 + tid; i < hl; i += NT) {
-      const double x = (double)S[i];
-      s = fma(x, x, s);
-    }
-    nrm_part[tid] = s;
-    if (tid == 0) sh_nrg = NT;
-  }
-  __syncthreads();
+  T* coefs = reinterpret_cast<T*>(nrm_part);  // per-column tau * w of the current step
 
   for (int j = 0; j < n; ++j) {
     T* colj = S + j * ld;
-    // Phase C: reflector for column j, by one warp chosen round-robin so
-    // that the serial step does not always load the same SM sub-partition.
+    // Phase C: reflector for column j by one warp, chosen round-robin so the
+    // serial step does not always load the same SM sub-partition.  The
+    // squared norm of the tail is summed by the whole warp (full lanes).
     if (warp == (j % (NT / 32))) {
-      const int nrg = sh_nrg;
       double ssq = 0.0;
-      for (int g = lane; g < nrg; g += 32) ssq += nrm_part[g];
+      for (int i = j + 1 + lane; i < hl; i += 32) {
+        const double x = (double)colj[i];
+        ssq = fma(x, x, ssq);
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
       double scale = 0.0;
@@ -96,7 +91,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
     const int chunk = (rows + rg - 1) / rg;
     const int slot = tid % acols, g = tid / acols;
     const int c = j + 1 + slot;
-    int i0 = j + g * chunk;
+    const int i0 = j + g * chunk;
     const int i1 = min(i0 + chunk, hl);
     // Phase A: partial dot products u_j^T a_c over this thread's rows.
     if (g < rg) {
@@ -108,33 +103,27 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
         ++i;
       }
       for (; i < i1; ++i) s = fma(colj[i], cc[i], s);
-      part[g * acols + slot] = (double)s;
+      part[g * acols + slot] = s;
     }
     __syncthreads();
-    // Phase B: a_c -= tau_j w_c u_j; squared norm of column j+1's new tail.
+    // The rg partial sums of each column, once: coef_c = tau_j * w_c.
+    if (tid < acols) {
+      T w = T(0);
+      for (int gg = 0; gg < rg; ++gg) w += part[gg * acols + tid];
+      coefs[tid] = (T)tau_s[j] * w;
+    }
+    __syncthreads();
+    // Phase B: a_c -= coef_c u_j.
     if (g < rg) {
-      double w = 0.0;
-      for (int gg = 0; gg < rg; ++gg) w += part[gg * acols + slot];
-      const T coef = (T)(tau_s[j] * w);
+      const T coef = coefs[slot];
       T* cc = S + c * ld;
       int i = i0;
       if (i == j && i < i1) {
         cc[j] -= coef;
         ++i;
       }
-      if (slot == 0) {
-        double ssq = 0.0;
-        for (; i < i1; ++i) {
-          const T x = cc[i] - coef * colj[i];
-          cc[i] = x;
-          if (i > j + 1) ssq = fma((double)x, (double)x, ssq);
-        }
-        nrm_part[g] = ssq;
-      } else {
-        for (; i < i1; ++i) cc[i] -= coef * colj[i];
-      }
+      for (; i < i1; ++i) cc[i] -= coef * colj[i];
     }
-    if (tid == 0) sh_nrg = rg;
     __syncthreads();
   }
   __syncthreads();
@@ -144,14 +133,14 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   const int nb = (n + 1) / 2;
   const int ntiles = nb * (nb + 1) / 2;
   constexpr int kMaxTiles = (NMAX / 2) * (NMAX / 2 + 1) / 2 / NT + 1;
-  double zacc[kMaxTiles][4];
-  auto yv = [&](int i, int col) -> double {
-    if (col >= n || i < col) return 0.0;
-    return i == col ? 1.0 : (double)S[col * ld + i];
+  T zacc[kMaxTiles][4];
+  auto yv = [&](int i, int col) -> T {
+    if (col >= n || i < col) return T(0);
+    return i == col ? T(1) : S[col * ld + i];
   };
 #pragma unroll
   for (int k = 0; k < kMaxTiles; ++k) {
-    zacc[k][0] = zacc[k][1] = zacc[k][2] = zacc[k][3] = 0.0;
+    zacc[k][0] = zacc[k][1] = zacc[k][2] = zacc[k][3] = T(0);
     const int t = tid + k * NT;
     if (t < ntiles) {
       // t -> (P, Q) with P <= Q, ordered by Q so that the lanes of a warp
@@ -160,10 +149,10 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
       while ((Q + 1) * (Q + 2) / 2 <= t) ++Q;
       const int P = t - Q * (Q + 1) / 2;
       const int p0 = 2 * P, q0 = 2 * Q;
-      double z00 = 0, z01 = 0, z10 = 0, z11 = 0;
+      T z00 = T(0), z01 = T(0), z10 = T(0), z11 = T(0);
       for (int i = q0; i < hl; ++i) {
-        const double a0 = yv(i, p0), a1 = yv(i, p0 + 1);
-        const double b0 = yv(i, q0), b1 = yv(i, q0 + 1);
+        const T a0 = yv(i, p0), a1 = yv(i, p0 + 1);
+        const T b0 = yv(i, q0), b1 = yv(i, q0 + 1);
         z00 = fma(a0, b0, z00);
         z01 = fma(a0, b1, z01);
         z10 = fma(a1, b0, z10);
@@ -190,7 +179,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   // Tm = Z above the diagonal, tau on it, zero below.
   for (int idx = tid; idx < n * n; idx += NT) {
     const int p = idx % n, q = idx / n;
-    Tm[idx] = p == q ? tau_s[p] : 0.0;
+    Tm[idx] = p == q ? (T)tau_s[p] : T(0);
   }
   __syncthreads();
 #pragma unroll
@@ -210,7 +199,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   }
   __syncthreads();
   build_t_doubling(Tm, Wt, n);
-  for (int idx = tid; idx < n * n; idx += NT) Tg[idx] = (T)Tm[idx];
+  for (int idx = tid; idx < n * n; idx += NT) Tg[idx] = Tm[idx];
   __syncthreads();
 }
 

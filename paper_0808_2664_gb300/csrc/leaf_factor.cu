@@ -6,13 +6,14 @@
 // bulk updates.  The h x n leaf sits in shared memory, column-major with an
 // odd leading dimension so that threads walking different columns at the
 // same row hit different banks.  Per column j:
-//   C  one warp sums the partial squared norms of the tail, its lane 0 turns
-//      (alpha, ||tail||^2) into (beta, tau, scale), and the warp scales the
-//      tail into the Householder vector u_j (unit entry implicit);
+//   C  one warp computes the squared norm of the tail (all 32 lanes, FP64),
+//      its lane 0 turns (alpha, ||tail||^2) into (beta, tau, scale), and the
+//      warp scales the tail into the Householder vector u_j (unit entry
+//      implicit);
 //   A  dot products w_c = u_j^T a_c for the trailing columns c > j, rows
-//      split into groups whose partial sums go to shared memory;
-//   B  a_c -= tau_j w_c u_j, and the squared norm of the next column's tail,
-//      accumulated while that column is updated.
+//      split into groups whose partial sums go to shared memory, then one
+//      thread per column sums its partials into tau_j w_c;
+//   B  a_c -= tau_j w_c u_j.
 // Work is re-partitioned over all threads in every phase, so the shrinking
 // active block keeps every warp busy.  After the last column, the
 // compact-WY T of the leaf is built from Z = strictly-upper(Y^T Y) (a

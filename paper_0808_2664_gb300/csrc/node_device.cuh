@@ -17,12 +17,12 @@ __host__ __device__ inline int node_ld(int n) { return n | 1; }
 
 __host__ __device__ inline size_t node_tile_bytes(int n, int q, size_t elem) {
   size_t tile = align_up_n(elem * (size_t)q * n * node_ld(n), 16);
-  const size_t tm = align_up_n(sizeof(double) * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
+  const size_t tm = align_up_n(elem * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
   return tile > tm ? tile : tm;
 }
 
 __host__ __device__ inline size_t node_smem_bytes(int n, int q, size_t elem, int nt) {
-  return node_tile_bytes(n, q, elem) + sizeof(double) * (2 * (size_t)nt + n);
+  return node_tile_bytes(n, q, elem) + (elem + sizeof(double)) * (size_t)nt + sizeof(double) * (size_t)n;
 }
 
 // Factors one node: the nc upper-triangular n x n children stored
@@ -36,13 +36,11 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
                                 unsigned char* smem) {
   const int ld = node_ld(n);
   T* S = reinterpret_cast<T*>(smem);
-  double* part = reinterpret_cast<double*>(smem + node_tile_bytes(n, q, sizeof(T)));
-  double* nrm_part = part + NT;
-  double* tau_s = nrm_part + NT;
-  double* Tm = reinterpret_cast<double*>(smem);
-  double* Wt = Tm + (size_t)n * n;
-  __shared__ double sh_scale;
-  __shared__ int sh_nrg;
+  // Products (dots, T) in the storage type T; norms and reflector scalars in FP64.
+  T* part = reinterpret_cast<T*>(smem + node_tile_bytes(n, q, sizeof(T)));
+  double* tau_s = reinterpret_cast<double*>(part + NT) + NT;
+  T* Tm = reinterpret_cast<T*>(smem);
+  T* Wt = Tm + (size_t)n * n;
   const int tid = threadIdx.x;
   // Element (i, c) of block b.
   auto at = [&](int b, int c, int i) -> T& { return S[((size_t)b * n + c) * ld + i]; };
@@ -65,45 +63,33 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int b = 1; b < nc; ++b) {
-      const double x = (double)at(b, 0, 0);
-      s = fma(x, x, s);
-    }
-    nrm_part[0] = s;
-    sh_nrg = 1;
-  }
-  __syncthreads();
 
   for (int j = 0; j < n; ++j) {
     const int jr = j + 1;                  // rows 0..j of each lower block
     const int vrows = 1 + (nc - 1) * jr;   // virtual row 0 is row j of block 0
-    if (tid == 0) {
+    const int tail = (nc - 1) * jr;        // virtual rows 1..vrows-1
+    // Phase C: warp 0 sums the squared tail (all lanes, FP64), lane 0 forms
+    // the reflector, the warp scales the tail into u_j.
+    if (tid < 32) {
       double ssq = 0.0;
-      for (int g = 0; g < sh_nrg; ++g) ssq += nrm_part[g];
-      if (j > 0) {
-        // Row j of every lower block joins the tail of column j here.
-        for (int b = 1; b < nc; ++b) {
-          const double x = (double)at(b, j, j);
-          ssq = fma(x, x, ssq);
-        }
+      for (int v = tid; v < tail; v += 32) {
+        const double x = (double)at(1 + v / jr, j, v % jr);
+        ssq = fma(x, x, ssq);
       }
-      const double alpha = (double)at(0, j, j);
-      Reflector r = make_reflector(
-          alpha, ssq,
-          [&]() {
-            return scaled_norm((nc - 1) * jr, [&](int v) { return (double)at(1 + v / jr, j, v % jr); });
-          },
-          status);
-      tau_s[j] = r.tau;
-      sh_scale = r.scale;
-      at(0, j, j) = (T)r.beta;
-    }
-    __syncthreads();
-    {
-      const double scale = sh_scale;
-      for (int v = tid; v < (nc - 1) * jr; v += NT) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+      double scale = 0.0;
+      if (tid == 0) {
+        const double alpha = (double)at(0, j, j);
+        Reflector r = make_reflector(
+            alpha, ssq,
+            [&]() { return scaled_norm(tail, [&](int v) { return (double)at(1 + v / jr, j, v % jr); }); }, status);
+        tau_s[j] = r.tau;
+        scale = r.scale;
+        at(0, j, j) = (T)r.beta;
+      }
+      scale = __shfl_sync(0xffffffffu, scale, 0);
+      for (int v = tid; v < tail; v += 32) {
         T& x = at(1 + v / jr, j, v % jr);
         x = (T)((double)x * scale);
       }
@@ -141,11 +127,11 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
         }
       }
       for (int o = rga >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (slot < acols && g == 0) part[slot] = (double)s;
+      if (slot < acols && g == 0) part[slot] = s;
     }
     __syncthreads();
     // Phase B: z values for the T factor; trailing updates.
-    if (tid < j) To[tid + (int64_t)j * n] = (T)part[tid];
+    if (tid < j) To[tid + (int64_t)j * n] = part[tid];
     const int bcols = n - 1 - j;
     if (bcols > 0) {
       int rgb = NT / bcols;
@@ -157,10 +143,9 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
       const int slot = tid % bcols, g = tid / bcols;
       if (g < rgb) {
         const int c = j + 1 + slot;
-        const T coef = (T)(tau_s[j] * part[c - 1]);
+        const T coef = (T)tau_s[j] * part[c - 1];
         int v = g * chunk;
         const int v1 = min(v + chunk, vrows);
-        double ssq = 0.0;
         if (v == 0 && v < v1) {
           at(0, c, j) -= coef;
           ++v;
@@ -168,18 +153,14 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
         if (v < v1) {
           int b = 1 + (v - 1) / jr, i = (v - 1) % jr;
           for (; v < v1; ++v) {
-            T& x = at(b, c, i);
-            x -= coef * at(b, j, i);
-            if (slot == 0) ssq = fma((double)x, (double)x, ssq);
+            at(b, c, i) -= coef * at(b, j, i);
             if (++i == jr) {
               i = 0;
               ++b;
             }
           }
         }
-        if (slot == 0) nrm_part[g] = ssq;
       }
-      if (tid == 0) sh_nrg = rgb;
     }
     __syncthreads();
   }
@@ -198,11 +179,11 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
   __syncthreads();
   for (int64_t idx = tid; idx < nn; idx += NT) {
     const int p = (int)(idx % n), jj = (int)(idx / n);
-    Tm[idx] = p < jj ? (double)To[idx] : (p == jj ? tau_s[p] : 0.0);
+    Tm[idx] = p < jj ? To[idx] : (p == jj ? (T)tau_s[p] : T(0));
   }
   __syncthreads();
   build_t_doubling(Tm, Wt, n);
-  for (int64_t idx = tid; idx < nn; idx += NT) To[idx] = (T)Tm[idx];
+  for (int64_t idx = tid; idx < nn; idx += NT) To[idx] = Tm[idx];
   __syncthreads();
 }
 

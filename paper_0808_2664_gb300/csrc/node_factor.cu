@@ -9,7 +9,7 @@
 // QR; 2n^3/3 flops per binary node, Section 2.2).  The resulting Y of a node
 // is the q-1 upper triangles that replaced R_1..R_{q-1}.
 //
-// One CTA per node, triangles in shared memory.  The same C/S/A/B phases as
+// One CTA per node, triangles in shared memory.  The same C/A/B phases as
 // the leaf kernel run over the "virtual rows" of reflector j: row j of block
 // 0 followed by rows 0..j of blocks 1..q-1.
 #include <cuda_runtime.h>

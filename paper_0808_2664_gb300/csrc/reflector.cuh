@@ -77,15 +77,16 @@ __device__ __forceinline__ double scaled_norm(int len, Get get) {
 
 __device__ __forceinline__ int pow2_floor(int x) { return x <= 1 ? 1 : 1 << (31 - __clz(x)); }
 
-// Build the compact-WY T (upper triangular, n x n, column-major ld n, FP64
-// shared memory) in place.  On entry Tm holds tau on the diagonal, the
+// Build the compact-WY T (upper triangular, n x n, column-major ld n, shared
+// memory, in the product type T) in place.  On entry Tm holds tau on the diagonal, the
 // strictly upper part of Y^T Y above it (Tm(p, q) = y_p^T y_q) and zeros
 // below.  Schreiber and Van Loan (cited in Section 2.1) give, for two blocks
 // of reflectors, I - Y T Y^T with T = [T1, -T1 (Y1^T Y2) T2; 0, T2]; applying
 // that merge to aligned blocks of 1, 2, 4, ... columns builds T in log2(n)
 // levels of independent triangular products.  Wt needs n*n/2 doubles.  Every
 // thread of the block calls this.
-__device__ __forceinline__ void build_t_doubling(double* Tm, double* Wt, int n) {
+template <typename T>
+__device__ __forceinline__ void build_t_doubling(T* Tm, T* Wt, int n) {
   for (int b = 1; b < n; b *= 2) {
     const int npairs = (n + 2 * b - 1) / (2 * b);
     const int bb = b * b;
@@ -95,7 +96,7 @@ __device__ __forceinline__ void build_t_doubling(double* Tm, double* Wt, int n) 
       const int pl = rem % b, ql = rem / b;
       const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
       if (q >= n) continue;
-      double acc = 0.0;
+      T acc = T(0);
       for (int r = s + b; r <= q; ++r) acc = fma(Tm[p + r * n], Tm[r + q * n], acc);
       Wt[pair * bb + pl + ql * b] = acc;
     }
@@ -106,7 +107,7 @@ __device__ __forceinline__ void build_t_doubling(double* Tm, double* Wt, int n) 
       const int pl = rem % b, ql = rem / b;
       const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
       if (q >= n) continue;
-      double acc = 0.0;
+      T acc = T(0);
       for (int r = p; r < s + b; ++r) acc = fma(Tm[p + r * n], Wt[pair * bb + (r - s) + ql * b], acc);
       Tm[p + q * n] = -acc;
     }
