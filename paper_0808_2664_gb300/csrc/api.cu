@@ -81,6 +81,10 @@ struct caqr_q_s {
   unsigned char* ws = nullptr;
   std::vector<tsqr_q_t> panels;
   int* status = nullptr;  // panel 0's status word
+  // Look-ahead: the next panel is factored on `side` while the rest of the
+  // trailing matrix is updated on the caller's stream.
+  cudaStream_t side = nullptr;
+  std::vector<cudaEvent_t> ev_left, ev_fact;
 };
 
 namespace {
@@ -548,7 +552,16 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
       rc = TSQR_ERR_NOMEM;
       break;
     }
-    rc = make_plan(p, m - j0, jb, TSQR_PREC_FP64, opts);
+    // Panels default to taller leaves than plain TSQR: the tree-node update
+    // work relative to the leaf update is n / (2h), and the panel factor
+    // is overlapped with the trailing update anyway.
+    tsqr_opts_t po = opts ? *opts : tsqr_opts_t{0, 0, 0};
+    if (po.leaf_rows == 0) {
+      int64_t h = 1;
+      while (h * 2 <= (160 * 1024 / 8) / jb && h * 2 <= 1024) h *= 2;
+      po.leaf_rows = h < jb ? jb : h;
+    }
+    rc = make_plan(p, m - j0, jb, TSQR_PREC_FP64, &po);
     if (rc == -4) rc = -5;
     plans.push_back(p);
     total += workspace_bytes(p);
@@ -573,6 +586,14 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
     cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
     if (e != cudaSuccess) rc = cuda_err(e);
   }
+  if (rc == TSQR_OK && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) rc = TSQR_ERR_CUDA;
+  c->ev_left.assign(c->panels.size(), nullptr);
+  c->ev_fact.assign(c->panels.size(), nullptr);
+  for (size_t j = 0; j < c->panels.size() && rc == TSQR_OK; ++j) {
+    if (cudaEventCreateWithFlags(&c->ev_left[j], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fact[j], cudaEventDisableTiming) != cudaSuccess)
+      rc = TSQR_ERR_CUDA;
+  }
   if (rc != TSQR_OK) {
     caqr_q_destroy(c);
     return rc;
@@ -588,18 +609,34 @@ int caqr_refactor(caqr_q_t c, double* A, int64_t lda, tsqr_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   c->A = A;
   c->lda = lda;
-  // Right-looking loop: TSQR of panel j, then (Q_j D_j)^T on the trailing columns.
-  for (size_t j = 0; j < c->panels.size(); ++j) {
+  // Right-looking loop with a look-ahead of one panel (Section 3's panel
+  // loop; the overlap is this implementation's): panel j+1's columns get
+  // (Q_j D_j)^T first, then panel j+1 is factored on the side stream while
+  // the remaining trailing columns are updated on the caller's stream.  The
+  // two touch disjoint columns of A.
+  const size_t np = c->panels.size();
+  int rc = refactor(c->panels[0], A, lda, A, lda, false, s);
+  if (rc != TSQR_OK) return rc;
+  for (size_t j = 0; j < np; ++j) {
     tsqr_q_s* p = c->panels[j];
     const int64_t j0 = (int64_t)j * c->b;
-    double* P = A + j0 + j0 * lda;
-    int rc = refactor(p, P, lda, P, lda, false, s);
+    const int64_t j1 = j0 + p->n;          // first trailing column
+    if (j + 1 == np) break;
+    tsqr_q_s* nx = c->panels[j + 1];
+    rc = apply_common(p, kApplyQT, nx->n, A + j0 + j1 * lda, lda, s);
     if (rc != TSQR_OK) return rc;
-    const int64_t kt = c->n - j0 - p->n;
+    if (cudaEventRecord(c->ev_left[j], s) != cudaSuccess) return TSQR_ERR_CUDA;
+    if (cudaStreamWaitEvent(c->side, c->ev_left[j], 0) != cudaSuccess) return TSQR_ERR_CUDA;
+    double* P = A + j1 + j1 * lda;
+    rc = refactor(nx, P, lda, P, lda, false, c->side);
+    if (rc != TSQR_OK) return rc;
+    if (cudaEventRecord(c->ev_fact[j + 1], c->side) != cudaSuccess) return TSQR_ERR_CUDA;
+    const int64_t kt = c->n - j1 - nx->n;
     if (kt > 0) {
-      rc = apply_common(p, kApplyQT, kt, A + j0 + (j0 + p->n) * lda, lda, s);
+      rc = apply_common(p, kApplyQT, kt, A + j0 + (j1 + nx->n) * lda, lda, s);
       if (rc != TSQR_OK) return rc;
     }
+    if (cudaStreamWaitEvent(s, c->ev_fact[j + 1], 0) != cudaSuccess) return TSQR_ERR_CUDA;
   }
   return TSQR_OK;
 }
@@ -717,6 +754,14 @@ int caqr_sync_status(caqr_q_t q, tsqr_stream_t stream) {
 int caqr_q_destroy(caqr_q_t q) {
   if (!valid(q)) return TSQR_ERR_HANDLE;
   q->magic = 0;
+  if (q->side) {
+    cudaStreamSynchronize(q->side);
+    cudaStreamDestroy(q->side);
+  }
+  for (auto e : q->ev_left)
+    if (e) cudaEventDestroy(e);
+  for (auto e : q->ev_fact)
+    if (e) cudaEventDestroy(e);
   for (auto* p : q->panels) destroy_handle(p);
   cudaError_t e = q->ws ? cudaFree(q->ws) : cudaSuccess;
   delete q;
