@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--variants", default="mixed,caqr,batched,grad", help="comma list of extra measurements")
+    p.add_argument("--caqr-leaf-rows", type=int, default=0)
     p.add_argument("--caqr-n", type=int, default=8192, help="square CAQR size for the CAQR variant")
     p.add_argument("--caqr-b", type=int, default=64)
     return p.parse_args()
@@ -211,7 +213,7 @@ def caqr_run(tq, torch, args, steps, warmup):
     g.manual_seed(3001)
     A0 = (torch.rand((n, n), generator=g, dtype=torch.float64, device=dev) * 2 - 1).t()
     A = tq.colmajor(n, n, torch.float64, dev)
-    q = tq.caqr_q_create(n, n, b, torch.float64, dev)
+    q = tq.caqr_q_create(n, n, b, torch.float64, dev, leaf_rows=args.caqr_leaf_rows)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -464,8 +466,10 @@ def ours(args, world, rank, local):
         e2e["value"] *= world
 
     variants = {}
-    if not args.no_variants:
-        del r["A0"], r["A"], r["Q"]
+    want = set() if args.no_variants else set(args.variants.split(","))
+    del r["A0"], r["A"], r["Q"]
+    torch.cuda.empty_cache()
+    if "mixed" in want:
         v = run_variant(tq, torch, args, torch.float32, max(3, args.steps), 3, seed=3000 + rank)
         variants["mixed_fp32_storage_fp64_reflectors"] = {
             "value": world * m / (v["ms_total"] / max(3, args.steps) / 1e3), "unit": "rows/s",
@@ -473,10 +477,13 @@ def ours(args, world, rank, local):
             "orthogonality": v["orth"], "status": v["status"]}
         del v
         torch.cuda.empty_cache()
+    if "caqr" in want:
         variants["caqr_fp64"] = caqr_run(tq, torch, args, steps=3, warmup=3)
         torch.cuda.empty_cache()
+    if "batched" in want:
         variants["batched_fp32_2048"] = batched_run(tq, torch, args, steps=5, warmup=3)
         torch.cuda.empty_cache()
+    if "grad" in want:
         variants["grad_fp64_1Mx128"] = grad_run(tq, torch, torch.float64, steps=3, warmup=3)
         variants["grad_fp32_1Mx128"] = grad_run(tq, torch, torch.float32, steps=3, warmup=3)
 

@@ -59,8 +59,11 @@ enum tsqr_status_code {
 };
 
 enum tsqr_precision {
-  TSQR_PREC_FP64 = 0, /* FP64 storage and arithmetic */
-  TSQR_PREC_FP32 = 1  /* FP32 storage and products; FP64 norms, vectors, tau */
+  TSQR_PREC_FP64 = 0,     /* FP64 storage and arithmetic */
+  TSQR_PREC_FP32 = 1,     /* FP32 storage and products; FP64 norms, vectors, tau */
+  TSQR_UPDATE_BF16X3 = 2  /* CAQR only: FP32 storage; leaf-block trailing updates on the
+                             tensor cores as three BF16 products (hi*hi + hi*lo + lo*hi)
+                             accumulated in FP32; FP64 norms, vectors, tau */
 };
 
 /* Tuning knobs; a zero field means "choose automatically". */
@@ -167,23 +170,26 @@ int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t lda, double* 
  *   A (device, m x n, lda >= m, m >= n) is overwritten by R in its upper
  *   triangle (diag(R) >= 0) and the panels' leaf Householder vectors below.
  *   b is the panel width (1 <= b; the last panel may be narrower).
- *   update_precision: TSQR_PREC_FP64 only for FP64 storage.
+ *   update_precision: TSQR_PREC_FP64 (caqr_factor, double storage), or
+ *   TSQR_PREC_FP32 / TSQR_UPDATE_BF16X3 (caqr_factor_f32, float storage).
  * For panel j the trailing columns receive (Q_j D_j)^T: first the leaf
  * blocks, then the tree nodes on stacked b-row slices (Section 3.1), then
  * the panel's signs, so rows of R stay consistent without a later fix.
  */
 int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
                 const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream);
+int caqr_factor_f32(int64_t m, int64_t n, float* A, int64_t lda, int64_t b, int32_t update_precision,
+                    const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream);
 
 /*
  * Plan-once form of CAQR: caqr_q_create plans every panel of an m x n
  * problem with panel width b and allocates all panel workspaces at once;
- * caqr_refactor then factors a matrix of that shape (device, lda >= m) in
- * place with no allocation.  caqr_factor = create + refactor.
+ * caqr_refactor then factors a matrix of that shape (device, lda >= m; double
+ * for TSQR_PREC_FP64, float otherwise) in place with no allocation.  caqr_factor = create + refactor.
  */
 int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, const tsqr_opts_t* opts,
                   caqr_q_t* q, tsqr_stream_t stream);
-int caqr_refactor(caqr_q_t q, double* A, int64_t lda, tsqr_stream_t stream);
+int caqr_refactor(caqr_q_t q, void* A, int64_t lda, tsqr_stream_t stream);
 
 /* caqr_apply_qt: C (m x k, ldc >= m) <- Q^T C, panels in factorisation order. */
 int caqr_apply_qt(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream);

@@ -17,11 +17,12 @@ from ._lib import TsqrBatchOpts, TsqrError, TsqrOpts, check, lib
 
 __all__ = [
     "TsqrError", "QTree", "CaqrQ", "colmajor", "as_colmajor", "tsqr_factor", "tsqr_q_create",
-    "caqr_factor", "caqr_q_create", "Batch", "PREC_FP64", "PREC_FP32",
+    "caqr_factor", "caqr_q_create", "Batch", "PREC_FP64", "PREC_FP32", "UPDATE_BF16X3",
 ]
 
 PREC_FP64 = 0
 PREC_FP32 = 1
+UPDATE_BF16X3 = 2
 
 
 def _torch():
@@ -262,6 +263,8 @@ def caqr_q_create(m: int, n: int, b: int = 64, dtype=None, device="cuda", update
     """Plan and allocate a CAQR handle; factor with CaqrQ.refactor."""
     torch = _torch()
     dtype = dtype or torch.float64
+    if dtype == torch.float32 and update_precision == PREC_FP64:
+        update_precision = PREC_FP32
     h = ctypes.c_void_p()
     o = _opts(leaf_rows, arity)
     check(lib().caqr_q_create(m, n, b, update_precision, ctypes.byref(o), ctypes.byref(h),
@@ -269,76 +272,24 @@ def caqr_q_create(m: int, n: int, b: int = 64, dtype=None, device="cuda", update
     return CaqrQ(h, m, n, dtype, None)
 
 
-def caqr_factor(A, b: int = 64, update_precision: int = PREC_FP64, leaf_rows: int = 0, arity: int = 0,
+def caqr_factor(A, b: int = 64, update_precision=None, leaf_rows: int = 0, arity: int = 0,
                 keep_q: bool = True):
-    """CAQR of the column-major m x n CUDA tensor A in place: R lands in A's upper triangle."""
+    """CAQR of the column-major m x n CUDA tensor A in place: R lands in A's upper triangle.
+
+    float64 tensors use the FP64 path; float32 tensors use FP32 storage with
+    FP64 reflector generation and, for their trailing updates, FP32 products
+    (``PREC_FP32``, default) or three BF16 tensor-core products (``UPDATE_BF16X3``).
+    """
+    torch = _torch()
     m, n = A.shape
     h = ctypes.c_void_p()
     o = _opts(leaf_rows, arity)
-    check(lib().caqr_factor(m, n, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), b, update_precision, ctypes.byref(o),
-                            ctypes.byref(h) if keep_q else None, _stream(A)), "caqr_factor")
+    if A.dtype == torch.float64:
+        upd = PREC_FP64 if update_precision is None else update_precision
+        fn = lib().caqr_factor
+    else:
+        upd = PREC_FP32 if update_precision is None else update_precision
+        fn = lib().caqr_factor_f32
+    check(fn(m, n, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), b, upd, ctypes.byref(o),
+             ctypes.byref(h) if keep_q else None, _stream(A)), "caqr_factor")
     return CaqrQ(h, m, n, A.dtype, A) if keep_q and h.value else None
-
-
-class Batch:
-    """Batched uneven TSQR bound to a list of column-major CUDA matrices.
-
-    ``factor()`` factors all of them in one persistent kernel launch (replayed
-    from a CUDA graph by default); each R lands in ``self.R[i]``.
-    """
-
-    def __init__(self, As, Rs=None, tile_kb: int = 0, arity: int = 0, autotune: bool = False):
-        torch = _torch()
-        if not As:
-            raise ValueError("empty batch")
-        self.dtype = As[0].dtype
-        self.A = list(As)
-        cnt = len(As)
-        if Rs is None:
-            Rs = [colmajor(a.shape[1], a.shape[1], self.dtype, a.device) for a in As]
-        self.R = list(Rs)
-        m = (ctypes.c_int64 * cnt)(*[a.shape[0] for a in As])
-        n = (ctypes.c_int64 * cnt)(*[a.shape[1] for a in As])
-        lda = (ctypes.c_int64 * cnt)(*[_ld(a, "A") for a in As])
-        ldr = (ctypes.c_int64 * cnt)(*[_ld(r, "R") for r in Rs])
-        Ap = (ctypes.c_void_p * cnt)(*[a.data_ptr() for a in As])
-        Rp = (ctypes.c_void_p * cnt)(*[r.data_ptr() for r in Rs])
-        for a in As:
-            if a.dtype != self.dtype:
-                raise TypeError("all matrices of a batch share one dtype")
-        o = TsqrBatchOpts(int(tile_kb), int(arity), 1 if autotune else 0, 0)
-        h = ctypes.c_void_p()
-        check(lib().tsqr_batch_create(cnt, m, n, Ap, lda, Rp, ldr, _prec(self.dtype), ctypes.byref(o),
-                                      ctypes.byref(h), _stream(As[0])), "tsqr_batch_create")
-        self._ptr = h
-
-    @property
-    def ptr(self):
-        if not self._ptr:
-            raise RuntimeError("handle already destroyed")
-        return self._ptr
-
-    def factor(self, graph: bool = True):
-        fn = lib().tsqr_batch_factor_graph if graph else lib().tsqr_batch_factor
-        check(fn(self.ptr, _stream(self.A[0])), "tsqr_batch_factor")
-        return self.R
-
-    def info(self) -> dict:
-        kb, q, it, ws = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
-        check(lib().tsqr_batch_info(self.ptr, ctypes.byref(kb), ctypes.byref(q), ctypes.byref(it), ctypes.byref(ws)),
-              "tsqr_batch_info")
-        return {"tile_kb": kb.value, "arity": q.value, "items": it.value, "workspace_bytes": ws.value}
-
-    def sync_status(self) -> int:
-        return lib().tsqr_batch_sync_status(self.ptr, _stream(self.A[0]))
-
-    def destroy(self):
-        if self._ptr:
-            lib().tsqr_batch_destroy(self._ptr)
-            self._ptr = None
-
-    def __del__(self):
-        try:
-            self.destroy()
-        except Exception:
-            pass

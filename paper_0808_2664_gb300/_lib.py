@@ -42,6 +42,7 @@ SIGNATURES = {
     "tsqr_q_destroy": ([vp], ctypes.c_int),
     "tsqr_factor_r_noalloc": ([i64, i64, vp, i64, vp, i64, vp], ctypes.c_int),
     "caqr_factor": ([i64, i64, vp, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
+    "caqr_factor_f32": ([i64, i64, vp, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
     "caqr_q_create": ([i64, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
     "caqr_refactor": ([vp, vp, i64, vp], ctypes.c_int),
     "caqr_apply_qt": ([vp, i64, vp, i64, vp], ctypes.c_int),

@@ -69,6 +69,8 @@ struct tsqr_q_s {
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events[TSQR_NUM_STAGES];
   int64_t launches[TSQR_NUM_STAGES] = {0, 0, 0, 0};
+  // Arithmetic of the leaf-block Q^T products (CAQR trailing updates).
+  int32_t upd = TSQR_PREC_FP64;
 };
 
 struct caqr_q_s {
@@ -85,6 +87,7 @@ struct caqr_q_s {
   // trailing matrix is updated on the caller's stream.
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> ev_left, ev_fact;
+  int32_t upd = TSQR_PREC_FP64;  // trailing-update arithmetic
 };
 
 namespace {
@@ -293,7 +296,15 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
   auto leaf = [&](int md) {
     StageTimer t(q, TSQR_STAGE_LEAF_APPLY, s);
     la.mode = md;
-    cudaError_t r = launch_leaf_apply(la, s);
+    cudaError_t r;
+    if constexpr (sizeof(T) == 4) {
+      if (md == kApplyQT && q->upd == TSQR_UPDATE_BF16X3)
+        r = launch_leaf_update_bf16x3(la, q->status, s);
+      else
+        r = launch_leaf_apply(la, s);
+    } else {
+      r = launch_leaf_apply(la, s);
+    }
     if (r == cudaSuccess) t.stop(1);
     return r;
   };
@@ -535,12 +546,17 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
   if (m < 1) return -1;
   if (n < 1 || n > m) return -2;
   if (b < 1) return -3;
-  if (update_precision != TSQR_PREC_FP64) return -4;
+  if (update_precision != TSQR_PREC_FP64 && update_precision != TSQR_PREC_FP32 &&
+      update_precision != TSQR_UPDATE_BF16X3)
+    return -4;
   caqr_q_s* c = new (std::nothrow) caqr_q_s();
   if (!c) return TSQR_ERR_NOMEM;
   c->m = m;
   c->n = n;
   c->b = b;
+  c->prec = update_precision == TSQR_PREC_FP64 ? TSQR_PREC_FP64 : TSQR_PREC_FP32;
+  c->es = c->prec == TSQR_PREC_FP64 ? 8 : 4;
+  c->upd = update_precision;
   // Plan every panel, then one allocation for all of their workspaces.
   std::vector<tsqr_q_s*> plans;
   size_t total = 0;
@@ -558,10 +574,12 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
     tsqr_opts_t po = opts ? *opts : tsqr_opts_t{0, 0, 0};
     if (po.leaf_rows == 0) {
       int64_t h = 1;
-      while (h * 2 <= (160 * 1024 / 8) / jb && h * 2 <= 1024) h *= 2;
+      const int64_t cap = update_precision == TSQR_UPDATE_BF16X3 ? kBf16x3MaxLeaf : 1024;
+      while (h * 2 <= (160 * 1024 / (int64_t)c->es) / jb && h * 2 <= cap) h *= 2;
       po.leaf_rows = h < jb ? jb : h;
     }
-    rc = make_plan(p, m - j0, jb, TSQR_PREC_FP64, &po);
+    rc = make_plan(p, m - j0, jb, c->prec, &po);
+    p->upd = update_precision;
     if (rc == -4) rc = -5;
     plans.push_back(p);
     total += workspace_bytes(p);
@@ -602,7 +620,7 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
   return TSQR_OK;
 }
 
-int caqr_refactor(caqr_q_t c, double* A, int64_t lda, tsqr_stream_t stream) {
+int caqr_refactor(caqr_q_t c, void* A, int64_t lda, tsqr_stream_t stream) {
   if (!valid(c)) return TSQR_ERR_HANDLE;
   if (!A) return -2;
   if (lda < c->m) return -3;
@@ -615,6 +633,8 @@ int caqr_refactor(caqr_q_t c, double* A, int64_t lda, tsqr_stream_t stream) {
   // the remaining trailing columns are updated on the caller's stream.  The
   // two touch disjoint columns of A.
   const size_t np = c->panels.size();
+  const size_t es = c->es;
+  auto at = [&](int64_t i, int64_t j) -> void* { return (unsigned char*)A + (size_t)(i + j * lda) * es; };
   int rc = refactor(c->panels[0], A, lda, A, lda, false, s);
   if (rc != TSQR_OK) return rc;
   for (size_t j = 0; j < np; ++j) {
@@ -623,17 +643,17 @@ int caqr_refactor(caqr_q_t c, double* A, int64_t lda, tsqr_stream_t stream) {
     const int64_t j1 = j0 + p->n;          // first trailing column
     if (j + 1 == np) break;
     tsqr_q_s* nx = c->panels[j + 1];
-    rc = apply_common(p, kApplyQT, nx->n, A + j0 + j1 * lda, lda, s);
+    rc = apply_common(p, kApplyQT, nx->n, at(j0, j1), lda, s);
     if (rc != TSQR_OK) return rc;
     if (cudaEventRecord(c->ev_left[j], s) != cudaSuccess) return TSQR_ERR_CUDA;
     if (cudaStreamWaitEvent(c->side, c->ev_left[j], 0) != cudaSuccess) return TSQR_ERR_CUDA;
-    double* P = A + j1 + j1 * lda;
+    void* P = at(j1, j1);
     rc = refactor(nx, P, lda, P, lda, false, c->side);
     if (rc != TSQR_OK) return rc;
     if (cudaEventRecord(c->ev_fact[j + 1], c->side) != cudaSuccess) return TSQR_ERR_CUDA;
     const int64_t kt = c->n - j1 - nx->n;
     if (kt > 0) {
-      rc = apply_common(p, kApplyQT, kt, A + j0 + (j1 + nx->n) * lda, lda, s);
+      rc = apply_common(p, kApplyQT, kt, at(j0, j1 + nx->n), lda, s);
       if (rc != TSQR_OK) return rc;
     }
     if (cudaStreamWaitEvent(s, c->ev_fact[j + 1], 0) != cudaSuccess) return TSQR_ERR_CUDA;
@@ -641,17 +661,9 @@ int caqr_refactor(caqr_q_t c, double* A, int64_t lda, tsqr_stream_t stream) {
   return TSQR_OK;
 }
 
-int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
-                const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
+static int caqr_factor_any(int64_t m, int64_t n, void* A, int64_t lda, int64_t b, int32_t update_precision,
+                           const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (q) *q = nullptr;
-  if (m < 0) return -1;
-  if (n < 0 || n > m) return -2;
-  if (m > 0 && n > 0 && !A) return -3;
-  if (lda < (m > 1 ? m : 1)) return -4;
-  if (b < 1) return -5;
-  if (update_precision != TSQR_PREC_FP64) return -6;
-  if (m == 0 || n == 0) return TSQR_OK;
   caqr_q_t c = nullptr;
   int rc = caqr_q_create(m, n, b, update_precision, opts, &c, stream);
   if (rc != TSQR_OK) return rc == -5 ? -7 : rc;
@@ -665,6 +677,32 @@ int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t
   return TSQR_OK;
 }
 
+int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
+                const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
+  if (q) *q = nullptr;
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (m > 0 && n > 0 && !A) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (b < 1) return -5;
+  if (update_precision != TSQR_PREC_FP64) return -6;
+  if (m == 0 || n == 0) return TSQR_OK;
+  return caqr_factor_any(m, n, A, lda, b, update_precision, opts, q, stream);
+}
+
+int caqr_factor_f32(int64_t m, int64_t n, float* A, int64_t lda, int64_t b, int32_t update_precision,
+                    const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
+  if (q) *q = nullptr;
+  if (m < 0) return -1;
+  if (n < 0 || n > m) return -2;
+  if (m > 0 && n > 0 && !A) return -3;
+  if (lda < (m > 1 ? m : 1)) return -4;
+  if (b < 1) return -5;
+  if (update_precision != TSQR_PREC_FP32 && update_precision != TSQR_UPDATE_BF16X3) return -6;
+  if (m == 0 || n == 0) return TSQR_OK;
+  return caqr_factor_any(m, n, A, lda, b, update_precision, opts, q, stream);
+}
+
 int caqr_apply_qt(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stream) {
   if (!valid(q)) return TSQR_ERR_HANDLE;
   if (k < 0) return -2;
@@ -673,7 +711,7 @@ int caqr_apply_qt(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t str
   if (ldc < q->m) return -4;
   for (size_t j = 0; j < q->panels.size(); ++j) {
     const int64_t j0 = (int64_t)j * q->b;
-    int rc = apply_common(q->panels[j], kApplyQT, k, (double*)C + j0, ldc, (cudaStream_t)stream);
+    int rc = apply_common(q->panels[j], kApplyQT, k, (unsigned char*)C + j0 * q->es, ldc, (cudaStream_t)stream);
     if (rc != TSQR_OK) return rc;
   }
   return TSQR_OK;
@@ -687,7 +725,7 @@ int caqr_apply_q(caqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stre
   if (ldc < q->m) return -4;
   for (size_t j = q->panels.size(); j-- > 0;) {
     const int64_t j0 = (int64_t)j * q->b;
-    int rc = apply_common(q->panels[j], kApplyQ, k, (double*)C + j0, ldc, (cudaStream_t)stream);
+    int rc = apply_common(q->panels[j], kApplyQ, k, (unsigned char*)C + j0 * q->es, ldc, (cudaStream_t)stream);
     if (rc != TSQR_OK) return rc;
   }
   return TSQR_OK;
@@ -701,13 +739,14 @@ int caqr_form_q(caqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   // Q = Q_0 diag(I, Q_1) diag(I, Q_2) ... [I_n; 0]: start from [I_n; 0] and
   // apply the panels last to first, each to the columns it can reach.
-  cudaError_t e = cudaMemset2DAsync(Q, ldq * sizeof(double), 0, q->m * sizeof(double), q->n, s);
+  cudaError_t e = cudaMemset2DAsync(Q, ldq * q->es, 0, q->m * q->es, q->n, s);
   if (e != cudaSuccess) return cuda_err(e);
-  e = launch_init_form<double>((double*)Q, ldq, (int)q->n, nullptr, s);
+  e = q->prec == TSQR_PREC_FP64 ? launch_init_form<double>((double*)Q, ldq, (int)q->n, nullptr, s)
+                                : launch_init_form<float>((float*)Q, ldq, (int)q->n, nullptr, s);
   if (e != cudaSuccess) return cuda_err(e);
   for (size_t j = q->panels.size(); j-- > 0;) {
     const int64_t j0 = (int64_t)j * q->b;
-    int rc = apply_common(q->panels[j], kApplyQ, q->n - j0, (double*)Q + j0 + j0 * ldq, ldq, s);
+    int rc = apply_common(q->panels[j], kApplyQ, q->n - j0, (unsigned char*)Q + (size_t)(j0 + j0 * ldq) * q->es, ldq, s);
     if (rc != TSQR_OK) return rc;
   }
   return TSQR_OK;

@@ -1,0 +1,331 @@
+// Leaf-block trailing update of CAQR on the 5th-generation tensor cores.
+//
+// For every leaf i of a panel (h_i <= 256 rows, n <= 64 reflectors) and a
+// 128-column slice of the trailing matrix C (FP32 storage), one CTA computes
+//     C_i <- C_i - Y_i (T_i^T (Y_i^T C_i))
+// (the leaf phase of Section 3.1's trailing update, Q_i^T in compact-WY
+// form).  The two products run on tcgen05.mma (kind::f16, BF16 inputs, FP32
+// accumulators in tensor memory).  Each FP32 operand x is split into two
+// BF16 terms, hi = bf16(x) and lo = bf16(x - hi), and every product is
+// formed as hi*hi + hi*lo + lo*hi ("3xBF16"); the dropped lo*lo term and the
+// split residuals leave about 2^-16 relative error per product.
+//   1. W^T = C^T Y   M = 128 (columns of C), N = n_pad, K = h in 64-row chunks
+//   2. W'^T = W^T T  FP32 on the CUDA cores, one column of C per thread
+//   3. D = Y W'      M = 128 rows per tile, N = 128, K = n_pad
+//   4. C -= D        epilogue from tensor memory, coalesced stores
+// Operands are staged by the CTA's threads into shared memory in the
+// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix);
+// one thread issues the MMAs, tcgen05.commit signals an mbarrier, and every
+// wait on that mbarrier gives up after a bounded number of polls (latching
+// the status word's timeout bit) so the kernel can never hang; tensor memory
+// is always released before the CTA exits.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tsqr_internal.cuh"
+
+namespace tsqr {
+namespace {
+
+constexpr int kUN = 128;       // columns of C per CTA (MMA M of step 1, N of step 3)
+constexpr int kUChunk = 64;    // leaf rows staged per step-1 chunk
+constexpr int kUThreads = 128; // four warps: one TMEM lane quarter each
+constexpr int kUNp = 64;       // reflector count padded to the MMA N / K granularity
+constexpr int kTmemCols = 256; // D1 at columns [0, 64), D2 at [64, 192)
+constexpr long long kPollLimit = 1ll << 24;
+
+// Byte offset of element (r, k) in a K-major no-swizzle tile with R rows:
+// core matrices of 8 rows x 8 BF16 (128 contiguous bytes), R/8 of them per
+// 8-column K slab, K slabs one after another.
+__device__ __forceinline__ uint32_t kmaj(int r, int k, int R) {
+  return (uint32_t)((((k >> 3) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// Shared-memory matrix descriptor (no swizzle): start address, leading byte
+// offset (between K-adjacent core matrices), stride byte offset (between
+// 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor for kind::f16: FP32 D, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Polls the mbarrier for the given phase parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long long i = 0; i < kPollLimit; ++i) {
+    uint32_t done = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void split_store(unsigned char* hi_base, unsigned char* lo_base, uint32_t off, float x) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  *reinterpret_cast<__nv_bfloat16*>(hi_base + off) = h;
+  *reinterpret_cast<__nv_bfloat16*>(lo_base + off) = l;
+}
+
+struct Bf16x3Args {
+  const float* Y;  // factored panel storage: leaf reflectors
+  int64_t ldy;
+  int64_t m;
+  int n;
+  int64_t h;
+  int64_t nleaves;
+  const float* Tw;  // nleaves x (n x n)
+  float* C;
+  int64_t ldc;
+  int64_t k;
+  int* status;
+};
+
+// Shared memory map (bytes from a 1024-aligned base).
+constexpr uint32_t kOffA1 = 0;                         // C^T chunk hi | lo: 2 x 128x64 bf16
+constexpr uint32_t kSzA1 = kUN * kUChunk * 2;          // 16 KB per term
+constexpr uint32_t kOffB1 = kOffA1 + 2 * kSzA1;        // Y chunk hi | lo: 2 x 64x64 bf16
+constexpr uint32_t kSzB1 = kUNp * kUChunk * 2;         // 8 KB per term
+constexpr uint32_t kOffA3 = kOffB1 + 2 * kSzB1;        // Y row tile hi | lo: 2 x 128x64 bf16
+constexpr uint32_t kSzA3 = 128 * kUNp * 2;             // 16 KB per term
+constexpr uint32_t kOffB3 = kOffA3 + 2 * kSzA3;        // W' hi | lo: 2 x 128x64 bf16
+constexpr uint32_t kSzB3 = kUN * kUNp * 2;             // 16 KB per term
+constexpr uint32_t kOffT = kOffB3 + 2 * kSzB3;         // T: 64x64 fp32
+constexpr uint32_t kOffBar = kOffT + kUNp * kUNp * 4;  // mbarrier (8 B) + tmem address (4 B)
+constexpr uint32_t kSmemBytes = kOffBar + 64 + 1024;   // + alignment slack
+
+__global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = a.n;
+  const int64_t leaf = blockIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.y * kUN;
+  const int kc = (int)((a.k - k0) < kUN ? (a.k - k0) : kUN);
+  const int64_t r0 = leaf * a.h;
+  const int hl = (leaf == a.nleaves - 1) ? (int)(a.m - r0) : (int)a.h;
+  const float* Yg = a.Y + r0;
+  float* Cg = a.C + r0 + k0 * a.ldc;
+  float* Ts = reinterpret_cast<float*>(sm + kOffT);
+  const uint32_t mbar = sbase + kOffBar;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 8);
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + kOffBar + 8),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // T of this leaf, zero-padded to 64 x 64.
+  const float* Tg = a.Tw + leaf * (int64_t)n * n;
+  for (int idx = tid; idx < kUNp * kUNp; idx += kUThreads) {
+    const int p = idx % kUNp, q = idx / kUNp;
+    Ts[idx] = (p < n && q < n) ? Tg[p + q * n] : 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t d1 = tmem, d2 = tmem + kUNp;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  auto yval = [&](int row, int p) -> float {
+    if (p >= n || row >= hl || row < p) return 0.f;
+    return row == p ? 1.f : Yg[row + (int64_t)p * a.ldy];
+  };
+
+  // ---- Step 1: W^T = C^T Y over the leaf rows, 64 rows per chunk.
+  const int nchunks = (hl + kUChunk - 1) / kUChunk;
+  for (int ch = 0; ch < nchunks && ok; ++ch) {
+    const int rb = ch * kUChunk;
+    for (int idx = tid; idx < kUN * kUChunk; idx += kUThreads) {
+      const int kk = idx % kUChunk, c = idx / kUChunk;  // consecutive threads walk rows (coalesced)
+      const int row = rb + kk;
+      const float x = (row < hl && c < kc) ? Cg[row + (int64_t)c * a.ldc] : 0.f;
+      split_store(sm + kOffA1, sm + kOffA1 + kSzA1, kmaj(c, kk, kUN), x);
+    }
+    for (int idx = tid; idx < kUNp * kUChunk; idx += kUThreads) {
+      const int kk = idx % kUChunk, p = idx / kUChunk;
+      split_store(sm + kOffB1, sm + kOffB1 + kSzB1, kmaj(p, kk, kUNp), yval(rb + kk, p));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      constexpr uint32_t id1 = idesc_bf16(kUN, kUNp);
+#pragma unroll
+      for (int s = 0; s < kUChunk / 16; ++s) {
+        const uint32_t aoff = (uint32_t)s * kUN * 32, boff = (uint32_t)s * kUNp * 32;
+        const uint64_t ahi = sdesc(sbase + kOffA1 + aoff, kUN * 16, 128);
+        const uint64_t alo = sdesc(sbase + kOffA1 + kSzA1 + aoff, kUN * 16, 128);
+        const uint64_t bhi = sdesc(sbase + kOffB1 + boff, kUNp * 16, 128);
+        const uint64_t blo = sdesc(sbase + kOffB1 + kSzB1 + boff, kUNp * 16, 128);
+        mma_bf16(d1, ahi, bhi, id1, (ch > 0 || s > 0) ? 1u : 0u);
+        mma_bf16(d1, ahi, blo, id1, 1u);
+        mma_bf16(d1, alo, bhi, id1, 1u);
+      }
+      mma_commit(mbar);
+    }
+    if (mbar_wait(mbar, phase & 1)) {
+      ++phase;
+    } else {
+      ok = false;
+      if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+
+  // ---- Step 2: W'^T(c, :) = W^T(c, :) T, thread c = TMEM lane c.
+  if (ok) {
+    float w[kUNp];
+#pragma unroll
+    for (int q = 0; q < kUNp; q += 16) tmem_ld16(d1 + ((uint32_t)(warp * 32) << 16) + q, w + q);
+    const int c = tid;
+    float wp[kUNp];
+#pragma unroll
+    for (int q = 0; q < kUNp; ++q) wp[q] = 0.f;
+    // T is upper triangular: W'^T(c, q) = sum_{p <= q} W^T(c, p) T(p, q).
+#pragma unroll
+    for (int p = 0; p < kUNp; ++p) {
+#pragma unroll
+      for (int q = p; q < kUNp; ++q) wp[q] = fmaf(w[p], Ts[p + q * kUNp], wp[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kUNp; ++q) split_store(sm + kOffB3, sm + kOffB3 + kSzB3, kmaj(c, q, kUN), wp[q]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+
+  // ---- Steps 3-4: D = Y W' per 128-row tile, then C -= D.
+  const int ntiles = (hl + 127) / 128;
+  for (int t = 0; t < ntiles && ok; ++t) {
+    const int rt = t * 128;
+    for (int idx = tid; idx < 128 * kUNp; idx += kUThreads) {
+      const int rr = idx % 128, p = idx / 128;
+      split_store(sm + kOffA3, sm + kOffA3 + kSzA3, kmaj(rr, p, 128), yval(rt + rr, p));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      constexpr uint32_t id3 = idesc_bf16(128, kUN);
+#pragma unroll
+      for (int s = 0; s < kUNp / 16; ++s) {
+        const uint32_t aoff = (uint32_t)s * 128 * 32, boff = (uint32_t)s * kUN * 32;
+        const uint64_t ahi = sdesc(sbase + kOffA3 + aoff, 128 * 16, 128);
+        const uint64_t alo = sdesc(sbase + kOffA3 + kSzA3 + aoff, 128 * 16, 128);
+        const uint64_t bhi = sdesc(sbase + kOffB3 + boff, kUN * 16, 128);
+        const uint64_t blo = sdesc(sbase + kOffB3 + kSzB3 + boff, kUN * 16, 128);
+        mma_bf16(d2, ahi, bhi, id3, s > 0 ? 1u : 0u);
+        mma_bf16(d2, ahi, blo, id3, 1u);
+        mma_bf16(d2, alo, bhi, id3, 1u);
+      }
+      mma_commit(mbar);
+    }
+    if (mbar_wait(mbar, phase & 1)) {
+      ++phase;
+    } else {
+      ok = false;
+      if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int row = rt + tid;  // TMEM lane = row of this tile
+#pragma unroll 1
+      for (int c0 = 0; c0 < kUN; c0 += 16) {
+        float d[16];
+        tmem_ld16(d2 + ((uint32_t)(warp * 32) << 16) + c0, d);
+        if (row < hl) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int c = c0 + e;
+            if (c < kc) Cg[row + (int64_t)c * a.ldc] -= d[e];
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  (void)lane;
+  if (!ok) {
+    // The pending commit's phase never completed in time: give the in-flight
+    // MMAs one more bounded wait before tensor memory is released.
+    mbar_wait(mbar, phase & 1);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_leaf_update_bf16x3(const LeafApplyArgs<float>& la, int* status, cudaStream_t s) {
+  if (la.nleaves <= 0 || la.k <= 0 || la.n <= 0) return cudaSuccess;
+  if (la.n > kBf16x3MaxN) return cudaErrorInvalidValue;
+  Bf16x3Args a;
+  a.Y = la.Y;
+  a.ldy = la.ldy;
+  a.m = la.m;
+  a.n = la.n;
+  a.h = la.h;
+  a.nleaves = la.nleaves;
+  a.Tw = la.Tw;
+  a.C = la.C;
+  a.ldc = la.ldc;
+  a.k = la.k;
+  a.status = status;
+  cudaError_t e = cudaFuncSetAttribute(bf16x3_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+  if (e != cudaSuccess) return e;
+  const int64_t kchunks = (la.k + kUN - 1) / kUN;
+  if (kchunks > 65535 || la.nleaves > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)la.nleaves, (unsigned)kchunks);
+  bf16x3_update_kernel<<<grid, kUThreads, kSmemBytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tsqr

@@ -22,6 +22,9 @@ constexpr int kApplyCols = 64;
 constexpr int kApplyRows = 32;
 // Largest n the kernels are built for.
 constexpr int kMaxN = 128;
+// Largest leaf height and panel width of the BF16x3 tensor-core leaf update.
+constexpr int kBf16x3MaxLeaf = 256;
+constexpr int kBf16x3MaxN = 64;
 
 // Three apply modes: C <- Q^T C, C <- Q C, and "form": C <- Q [X; 0] where X
 // is read from the first n rows of the block and the rest of the block is
@@ -98,6 +101,9 @@ template <typename T>
 cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_node_apply(const NodeApplyArgs<T>& a, cudaStream_t s);
+
+// C <- C - Y T^T Y^T C per leaf with 3xBF16 tcgen05 products (FP32 storage, n <= 64).
+cudaError_t launch_leaf_update_bf16x3(const LeafApplyArgs<float>& a, int* status, cudaStream_t s);
 
 // d = sign(diag Rroot) (sign(0) = +1); Rout = D * triu(Rroot), ldr.  Entries
 // below the diagonal of Rout are zeroed when zero_lower, left alone otherwise.
