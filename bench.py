@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-variants", action="store_true")
-    p.add_argument("--variants", default="mixed,caqr,batched,grad", help="comma list of extra measurements")
+    p.add_argument("--variants", default="mixed,caqr,caqr_mixed,batched,grad",
+                   help="comma list of extra measurements")
     p.add_argument("--caqr-leaf-rows", type=int, default=0)
     p.add_argument("--caqr-n", type=int, default=8192, help="square CAQR size for the CAQR variant")
     p.add_argument("--caqr-b", type=int, default=64)
@@ -205,15 +206,21 @@ def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False):
             "q": q, "A0": A0, "A": A, "Q": Q, "R": R}
 
 
-def caqr_run(tq, torch, args, steps, warmup):
-    """Square FP64 CAQR, U[-1, 1] entries, panel width b: GFLOP/s of 4n^3/3 and the update's roofline."""
+def caqr_run(tq, torch, args, steps, warmup, dtype=None, upd=None):
+    """Square CAQR, U[-1, 1] entries, panel width b: GFLOP/s of 4n^3/3 and the update's roofline.
+
+    dtype float64 -> FP64 throughout; float32 -> FP32 storage with FP64
+    reflector generation and FP32 (upd = PREC_FP32) or 3xBF16 tensor-core
+    (upd = UPDATE_BF16X3) trailing updates."""
+    dtype = dtype or torch.float64
+    upd = tq.PREC_FP64 if upd is None else upd
     n, b = args.caqr_n, args.caqr_b
     dev = torch.device("cuda")
     g = torch.Generator(device=dev)
     g.manual_seed(3001)
-    A0 = (torch.rand((n, n), generator=g, dtype=torch.float64, device=dev) * 2 - 1).t()
-    A = tq.colmajor(n, n, torch.float64, dev)
-    q = tq.caqr_q_create(n, n, b, torch.float64, dev, leaf_rows=args.caqr_leaf_rows)
+    A0 = (torch.rand((n, n), generator=g, dtype=torch.float64, device=dev) * 2 - 1).to(dtype).t()
+    A = tq.colmajor(n, n, dtype, dev)
+    q = tq.caqr_q_create(n, n, b, dtype, dev, update_precision=upd, leaf_rows=args.caqr_leaf_rows)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -233,19 +240,36 @@ def caqr_run(tq, torch, args, steps, warmup):
     ms = e0.elapsed_time(e1) / steps
     st = q.stage_times()
     q.set_timing(False)
-    Q = q.form_q()
-    R = torch.triu(A)
-    berr = (torch.linalg.norm(A0 - Q @ R) / torch.linalg.norm(A0)).item()
+    Q = q.form_q().double()
+    R = torch.triu(A).double()
+    A64 = A0.double()
+    berr = (torch.linalg.norm(A64 - Q @ R) / torch.linalg.norm(A64)).item()
     orth = torch.linalg.norm(torch.eye(n, dtype=torch.float64, device=dev) - Q.t() @ Q).item()
     flops = 4.0 * n ** 3 / 3.0
     upd_ms = st["leaf_apply"][0] / steps
     upd_flops = sum(4.0 * (n - j) * b * (n - j - b) for j in range(0, n, b))
+    eps = {tq.PREC_FP64: 2.0 ** -52, tq.PREC_FP32: 2.0 ** -23, tq.UPDATE_BF16X3: 2.0 ** -16}[upd]
+    if upd == tq.UPDATE_BF16X3:
+        peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+        ach = 3 * upd_flops / (upd_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": "bf16x3_update_kernel (tcgen05, 3 BF16 products per FP32 product)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "note": "achieved counts the 3 BF16 products; the trailing matrix is re-read per panel, so HBM binds at b = 64"}
+    elif upd == tq.PREC_FP32:
+        ach = upd_flops / (upd_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "leaf_apply_kernel<float> (trailing update)", "achieved": ach,
+                "peak": 152 * 128 * 2 * 2.07e9 / 1e12, "unit": "TFLOP/s",
+                "frac": ach / (152 * 128 * 2 * 2.07e9 / 1e12)}
+    else:
+        ach = upd_flops / (upd_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "leaf_apply_kernel<double> (trailing update)", "achieved": ach,
+                "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": ach / (FP64_PEAK_GFLOPS / 1e3)}
     return {"value": flops / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "n": n, "b": b,
-            "update_precision": "fp64", "backward_error": berr, "orthogonality": orth,
-            "tolerance": 10 * n * 2.0 ** -52 * n ** 0.5, "status": q.sync_status(),
-            "update_roofline": {"bound": "alu", "kernel": "leaf_apply_kernel<double> (trailing update)",
-                                "achieved": upd_flops / (upd_ms / 1e3) / 1e12, "peak": FP64_PEAK_GFLOPS / 1e3,
-                                "unit": "TFLOP/s", "frac": upd_flops / (upd_ms / 1e3) / 1e12 / (FP64_PEAK_GFLOPS / 1e3)},
+            "storage": str(dtype).replace("torch.", ""),
+            "update_precision": {tq.PREC_FP64: "fp64", tq.PREC_FP32: "fp32", tq.UPDATE_BF16X3: "3xbf16"}[upd],
+            "backward_error": berr, "orthogonality": orth, "tolerance": 10 * n * eps * n ** 0.5,
+            "status": q.sync_status(), "update_roofline": roof,
             "stage_ms_per_step": {k: v[0] / steps for k, v in st.items()}}
 
 
@@ -479,6 +503,11 @@ def ours(args, world, rank, local):
         torch.cuda.empty_cache()
     if "caqr" in want:
         variants["caqr_fp64"] = caqr_run(tq, torch, args, steps=3, warmup=3)
+        torch.cuda.empty_cache()
+    if "caqr_mixed" in want:
+        variants["caqr_fp32_update"] = caqr_run(tq, torch, args, 3, 3, torch.float32, tq.PREC_FP32)
+        torch.cuda.empty_cache()
+        variants["caqr_3xbf16_update"] = caqr_run(tq, torch, args, 3, 3, torch.float32, tq.UPDATE_BF16X3)
         torch.cuda.empty_cache()
     if "batched" in want:
         variants["batched_fp32_2048"] = batched_run(tq, torch, args, steps=5, warmup=3)
