@@ -146,10 +146,9 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
   int64_t h = opts && opts->leaf_rows > 0 ? opts->leaf_rows : 0;
   if (h == 0) {
     // Largest power of two (at most 1024) whose n-column leaf tile stays
-    // within about 68 KB for FP64, so that three leaf CTAs share an SM and
-    // hide each other's serial reflector steps; FP32 leaves get 136 KB (one
-    // 256-thread CTA per SM, twice the rows per leaf).
-    const int64_t budget = (q->es == 8 ? 68 : 136) * 1024 / (int64_t)q->es;
+    // within about 68 KB, so that three leaf CTAs share an SM and hide each
+    // other's serial reflector steps.
+    const int64_t budget = 68 * 1024 / (int64_t)q->es;
     h = 1;
     while (h * 2 <= budget / n && h * 2 <= 1024) h *= 2;
     if (h < n) h = n;

@@ -47,9 +47,20 @@ __device__ __forceinline__ Reflector make_reflector(double alpha, double ssq, Re
     r.scale = 0.0;
     r.beta = alpha;
   } else {
+    // With d = alpha - beta (|d| = |alpha| + nrm, no cancellation) and one
+    // reciprocal rp = 1 / (beta d): scale = 1/d = beta rp and
+    // tau = (beta - alpha)/beta = -d/beta = -d^2 rp.
     r.beta = alpha >= 0.0 ? -nrm : nrm;
-    r.tau = (r.beta - alpha) / r.beta;
-    r.scale = 1.0 / (alpha - r.beta);
+    const double d = alpha - r.beta;
+    const double bd = r.beta * d;
+    if (isfinite(bd) && fabs(bd) > 1e-300) {
+      const double rp = 1.0 / bd;
+      r.scale = r.beta * rp;
+      r.tau = -(d * d) * rp;
+    } else {  // beta d over- or underflows: form the two quotients directly
+      r.tau = (r.beta - alpha) / r.beta;
+      r.scale = 1.0 / d;
+    }
   }
   if (!isfinite(r.beta) || !isfinite(r.tau) || !isfinite(alpha)) atomicOr(status, kStatusNonfinite);
   return r;
