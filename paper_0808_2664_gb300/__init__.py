@@ -293,3 +293,67 @@ def caqr_factor(A, b: int = 64, update_precision=None, leaf_rows: int = 0, arity
     check(fn(m, n, ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), b, upd, ctypes.byref(o),
              ctypes.byref(h) if keep_q else None, _stream(A)), "caqr_factor")
     return CaqrQ(h, m, n, A.dtype, A) if keep_q and h.value else None
+
+
+class Batch:
+    """Batched uneven TSQR bound to a list of column-major CUDA matrices.
+
+    ``factor()`` factors all of them in one persistent kernel launch (replayed
+    from a CUDA graph by default); each R lands in ``self.R[i]``.
+    """
+
+    def __init__(self, As, Rs=None, tile_kb: int = 0, arity: int = 0, autotune: bool = False):
+        torch = _torch()
+        if not As:
+            raise ValueError("empty batch")
+        self.dtype = As[0].dtype
+        self.A = list(As)
+        cnt = len(As)
+        if Rs is None:
+            Rs = [colmajor(a.shape[1], a.shape[1], self.dtype, a.device) for a in As]
+        self.R = list(Rs)
+        m = (ctypes.c_int64 * cnt)(*[a.shape[0] for a in As])
+        n = (ctypes.c_int64 * cnt)(*[a.shape[1] for a in As])
+        lda = (ctypes.c_int64 * cnt)(*[_ld(a, "A") for a in As])
+        ldr = (ctypes.c_int64 * cnt)(*[_ld(r, "R") for r in Rs])
+        Ap = (ctypes.c_void_p * cnt)(*[a.data_ptr() for a in As])
+        Rp = (ctypes.c_void_p * cnt)(*[r.data_ptr() for r in Rs])
+        for a in As:
+            if a.dtype != self.dtype:
+                raise TypeError("all matrices of a batch share one dtype")
+        o = TsqrBatchOpts(int(tile_kb), int(arity), 1 if autotune else 0, 0)
+        h = ctypes.c_void_p()
+        check(lib().tsqr_batch_create(cnt, m, n, Ap, lda, Rp, ldr, _prec(self.dtype), ctypes.byref(o),
+                                      ctypes.byref(h), _stream(As[0])), "tsqr_batch_create")
+        self._ptr = h
+
+    @property
+    def ptr(self):
+        if not self._ptr:
+            raise RuntimeError("handle already destroyed")
+        return self._ptr
+
+    def factor(self, graph: bool = True):
+        fn = lib().tsqr_batch_factor_graph if graph else lib().tsqr_batch_factor
+        check(fn(self.ptr, _stream(self.A[0])), "tsqr_batch_factor")
+        return self.R
+
+    def info(self) -> dict:
+        kb, q, it, ws = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().tsqr_batch_info(self.ptr, ctypes.byref(kb), ctypes.byref(q), ctypes.byref(it), ctypes.byref(ws)),
+              "tsqr_batch_info")
+        return {"tile_kb": kb.value, "arity": q.value, "items": it.value, "workspace_bytes": ws.value}
+
+    def sync_status(self) -> int:
+        return lib().tsqr_batch_sync_status(self.ptr, _stream(self.A[0]))
+
+    def destroy(self):
+        if self._ptr:
+            lib().tsqr_batch_destroy(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

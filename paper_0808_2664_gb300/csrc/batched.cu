@@ -60,7 +60,6 @@ template <typename T>
 struct BLevel {
   T* R;
   T* Y;
-  T* Tw;
   T* tau;
   int64_t items;
   int64_t counter_base;
@@ -143,7 +142,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchArgs<T> a) {
       __syncthreads();
       if (sh_ok) {
         node_factor_one<T, NT>(Rin + c0 * nn, nc, M.q, n, L.R + w.idx * nn, L.Y + w.idx * (int64_t)(M.q - 1) * nn,
-                               L.Tw + w.idx * nn, L.tau + w.idx * (int64_t)n, a.status, smem);
+                               L.tau + w.idx * (int64_t)n, a.status, smem);
       }
       done_r = L.R + w.idx * nn;
     }
@@ -264,8 +263,6 @@ int build_batch(tsqr_batch_s* b, const int64_t* m, const int64_t* n, void* const
       off += al256(its[l] * nnb);
       L.Y = (T*)off;
       off += al256(its[l] * (b->arity - 1) * nnb);
-      L.Tw = (T*)off;
-      off += al256(its[l] * nnb);
       L.tau = (T*)off;
       off += al256(its[l] * nvb);
       L.counter_base = ncounters;
@@ -325,7 +322,6 @@ int build_batch(tsqr_batch_s* b, const int64_t* m, const int64_t* n, void* const
   for (auto& L : levels) {
     L.R = rebase(L.R);
     L.Y = rebase(L.Y);
-    L.Tw = rebase(L.Tw);
     L.tau = rebase(L.tau);
   }
   b->ws = B;

@@ -16,9 +16,8 @@ __host__ __device__ inline size_t align_up_n(size_t x, size_t a) { return (x + a
 __host__ __device__ inline int node_ld(int n) { return n | 1; }
 
 __host__ __device__ inline size_t node_tile_bytes(int n, int q, size_t elem) {
-  size_t tile = align_up_n(elem * (size_t)q * n * node_ld(n), 16);
-  const size_t tm = align_up_n(elem * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
-  return tile > tm ? tile : tm;
+  const size_t tile = align_up_n(elem * (size_t)q * n * node_ld(n), 16);
+  return tile;
 }
 
 __host__ __device__ inline size_t node_smem_bytes(int n, int q, size_t elem, int nt) {
@@ -28,19 +27,18 @@ __host__ __device__ inline size_t node_smem_bytes(int n, int q, size_t elem, int
 // Factors one node: the nc upper-triangular n x n children stored
 // contiguously from Rin (ld n each; read with L1-bypassing loads so that a
 // child written by another CTA of the same launch is seen), arity q.  Writes
-// the node's R (Ro), its q-1 upper-triangular reflector blocks (Yo), tau
-// (tauo) and compact-WY T (To).  A lone child (nc = 1) passes through with
+// the node's R (Ro), its q-1 upper-triangular reflector blocks (Yo) and tau
+// (tauo).  Node reflectors are applied one by one (no compact-WY T): for the
+// structured Y of a node that costs fewer flops than the WY form.  A lone child (nc = 1) passes through with
 // an identity Q.  Every thread of the block calls it.
 template <typename T, int NT>
-__device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo, T* To, T* tauo, int* status,
+__device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo, T* tauo, int* status,
                                 unsigned char* smem) {
   const int ld = node_ld(n);
   T* S = reinterpret_cast<T*>(smem);
   // Products (dots, T) in the storage type T; norms and reflector scalars in FP64.
   T* part = reinterpret_cast<T*>(smem + node_tile_bytes(n, q, sizeof(T)));
   double* tau_s = reinterpret_cast<double*>(part + NT) + NT;
-  T* Tm = reinterpret_cast<T*>(smem);
-  T* Wt = Tm + (size_t)n * n;
   const int tid = threadIdx.x;
   // Element (i, c) of block b.
   auto at = [&](int b, int c, int i) -> T& { return S[((size_t)b * n + c) * ld + i]; };
@@ -49,7 +47,6 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
     // A lone child passes up unchanged: its Q factor is the identity.
     for (int64_t idx = tid; idx < nn; idx += NT) {
       Ro[idx] = __ldcg(Rin + idx);
-      To[idx] = T(0);
     }
     for (int64_t idx = tid; idx < (int64_t)(q - 1) * nn; idx += NT) Yo[idx] = T(0);
     for (int c = tid; c < n; c += NT) tauo[c] = T(0);
@@ -95,8 +92,8 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
       }
     }
     __syncthreads();
-    // Phase A: dot products of u_j with every other column.
-    const int acols = n - 1;
+    // Phase A: w_c = u_j^T a_c for the trailing columns c > j.
+    const int acols = n - 1 - j;
     if (acols > 0) {
       int lim = NT / acols;
       int byrows = vrows / kMinRowsNode;
@@ -108,7 +105,7 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
       const int slot = tid / rga, g = tid % rga;
       T s = T(0);
       if (slot < acols) {
-        const int c = slot < j ? slot : slot + 1;
+        const int c = j + 1 + slot;
         int v = g * chunk;
         const int v1 = min(v + chunk, vrows);
         if (v == 0 && v < v1) {
@@ -130,8 +127,7 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
       if (slot < acols && g == 0) part[slot] = s;
     }
     __syncthreads();
-    // Phase B: z values for the T factor; trailing updates.
-    if (tid < j) To[tid + (int64_t)j * n] = part[tid];
+    // Phase B: trailing updates a_c -= tau_j w_c u_j.
     const int bcols = n - 1 - j;
     if (bcols > 0) {
       int rgb = NT / bcols;
@@ -143,7 +139,7 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
       const int slot = tid % bcols, g = tid / bcols;
       if (g < rgb) {
         const int c = j + 1 + slot;
-        const T coef = (T)tau_s[j] * part[c - 1];
+        const T coef = (T)tau_s[j] * part[slot];
         int v = g * chunk;
         const int v1 = min(v + chunk, vrows);
         if (v == 0 && v < v1) {
@@ -176,14 +172,6 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
     }
   }
   for (int c = tid; c < n; c += NT) tauo[c] = (T)tau_s[c];
-  __syncthreads();
-  for (int64_t idx = tid; idx < nn; idx += NT) {
-    const int p = (int)(idx % n), jj = (int)(idx / n);
-    Tm[idx] = p < jj ? To[idx] : (p == jj ? (T)tau_s[p] : T(0));
-  }
-  __syncthreads();
-  build_t_doubling(Tm, Wt, n);
-  for (int64_t idx = tid; idx < nn; idx += NT) To[idx] = Tm[idx];
   __syncthreads();
 }
 

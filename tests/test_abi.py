@@ -66,3 +66,10 @@ def test_oracle_and_library_share_nothing():
         src = open(os.path.join(ROOT, "oracle", f)).read()
         deps = re.findall(r"(?:^|\n)\s*(?:import|from|#include)\s+[\"<]?([\w./]+)", src)
         assert not [d for d in deps if "paper_0808_2664_gb300" in d or "tsqr" in d], (f, deps)
+
+
+def test_binding_exports_every_public_name():
+    import paper_0808_2664_gb300 as tq
+
+    for name in tq.__all__:
+        assert hasattr(tq, name), name
