@@ -58,7 +58,7 @@ struct tsqr_q_s {
   void* leafR = nullptr;
   void* leafTau = nullptr;
   void* leafT = nullptr;
-  std::vector<void*> nodeR, nodeY, nodeTau;  // index l-1 for level l
+  std::vector<void*> nodeR, nodeY, nodeTau, nodeT;  // index l-1 for level l
   void* d = nullptr;
   int* status = nullptr;
   // The factored matrix (borrowed).
@@ -182,7 +182,7 @@ size_t workspace_bytes(const tsqr_q_s* q) {
   b += align_up(q->nleaves * nn) * 2 + align_up(q->nleaves * nv);
   for (int l = 1; l <= q->levels; ++l) {
     const size_t it = (size_t)q->items[l];
-    b += align_up(it * nn) + align_up(it * (q->q - 1) * nn) + align_up(it * nv);
+    b += align_up(it * nn) * 2 + align_up(it * (q->q - 1) * nn) + align_up(it * nv);
   }
   b += align_up(nv) + align_up(sizeof(int));
   return b;
@@ -203,9 +203,11 @@ void bind_workspace(tsqr_q_s* q, unsigned char* base) {
   q->nodeR.assign(q->levels, nullptr);
   q->nodeY.assign(q->levels, nullptr);
   q->nodeTau.assign(q->levels, nullptr);
+  q->nodeT.assign(q->levels, nullptr);
   for (int l = 1; l <= q->levels; ++l) {
     const size_t it = (size_t)q->items[l];
     q->nodeR[l - 1] = take(it * nn);
+    q->nodeT[l - 1] = take(it * nn);
     q->nodeY[l - 1] = take(it * (q->q - 1) * nn);
     q->nodeTau[l - 1] = take(it * nv);
   }
@@ -251,6 +253,7 @@ cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool z
     na.Rout = (T*)q->nodeR[l - 1];
     na.Y = (T*)q->nodeY[l - 1];
     na.tau = (T*)q->nodeTau[l - 1];
+    na.Tw = (T*)q->nodeT[l - 1];
     na.status = q->status;
     e = launch_node_factor(na, s);
     if (e != cudaSuccess) return e;
@@ -277,7 +280,7 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
   auto node = [&](int l, int md) {
     NodeApplyArgs<T> na{};
     na.Y = (const T*)q->nodeY[l - 1];
-    na.tau = (const T*)q->nodeTau[l - 1];
+    na.Tw = (const T*)q->nodeT[l - 1];
     na.nin = q->items[l - 1];
     na.arity = q->q;
     na.n = (int)q->n;

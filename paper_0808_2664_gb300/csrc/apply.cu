@@ -1,12 +1,11 @@
 // Implicit application of the tree-structured Q (Section 2.1,
 // Eq. TSQR_binarytree_4): Q = diag(Q_i) * (tree-node factors) * D.
 //
-// A leaf's factor is a compact-WY block reflector I - Y T Y^T (Schreiber and
-// Van Loan, cited in Section 2.1), applied to its h-row block of C:
+// Every factor is a compact-WY block reflector I - Y T Y^T (Schreiber and Van
+// Loan, cited in Section 2.1).  A leaf applies it to its h-row block of C:
 //   W = Y^T C,  W <- T^T W (for Q^T) or T W (for Q),  C <- C - Y W.
-// A tree node acts on the q stacked n-row "slots" of C that hold its
-// children's R rows; its reflectors u_j = [e_j; y_1j; ...] are applied one
-// at a time.
+// A tree node applies it to the q stacked n-row "slots" of C that hold its
+// children's R rows; its Y is [I; Y_1; ...; Y_{q-1}] with upper-triangular Y_b.
 // The "form" mode computes Q [X; 0] reading only X (the first n rows), which
 // is how the thin Q is built top-down without initialising the rest of Q.
 #include <cuda_runtime.h>
@@ -170,107 +169,109 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
 }
 
 // ----------------------------------------------------------------- nodes --
-// A tree node's Q is the product of its n reflectors H_j = I - tau_j u_j u_j^T
-// with u_j = [e_j; y_1j; ...; y_(q-1)j], y_bj being column j (rows 0..j) of
-// the upper-triangular block Y_b.  For this structure applying the
-// reflectors one at a time costs fewer flops than a compact-WY form, so node
-// Q's are applied that way: Q^T takes H_0 first, Q takes H_{n-1} first.
-// One CTA per (node, slice of kcw columns of C); the nc slots (n rows each)
-// and the node's Y blocks sit in shared memory; per reflector the threads
-// split (column, row group), reduce the row-group partial dots through shared
-// memory, then update.  Form mode starts from slot 0 = X and zero lower slots.
+// Shared memory (column-major tiles, ldn odd): B1 [kc][ldn] holds a lower
+// slot while W accumulates and then W' = T^(T) W; B2 [kc][ldn] holds W and
+// later Y_b W'; Ys [n][ldn] one lower block of Y; Ts [n][n].
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n = a.n, q = a.arity, kcw = a.kc_chunk;
+  constexpr int KC = kApplyCols;
+  const int n = a.n, q = a.arity;
   const int ldn = n | 1;
-  T* Sl = reinterpret_cast<T*>(smem);                   // q slots x kcw columns x ldn
-  T* Ys = Sl + (size_t)q * kcw * ldn;                   // (q-1) blocks x n columns x ldn
-  T* part = Ys + (size_t)(q - 1) * n * ldn;             // NT partial dots
+  T* B1 = reinterpret_cast<T*>(smem);
+  T* B2 = B1 + (size_t)KC * ldn;
+  T* Ys = B2 + (size_t)KC * ldn;
+  T* Ts = Ys + (size_t)n * ldn;
   const int tid = threadIdx.x;
   const int64_t node = blockIdx.x;
   const int64_t c0 = node * q;
   const int nc = (int)((a.nin - c0) < q ? (a.nin - c0) : q);
   if (nc <= 1) return;  // a lone child: identity
-  const int64_t k0 = (int64_t)blockIdx.y * kcw;
-  const int kc = (int)((a.k - k0) < kcw ? (a.k - k0) : kcw);
+  const int64_t k0 = (int64_t)blockIdx.y * KC;
+  const int kc = (int)((a.k - k0) < KC ? (a.k - k0) : KC);
   const int64_t nn = (int64_t)n * n;
   const T* Yn = a.Y + node * (int64_t)(q - 1) * nn;
-  const T* taun = a.tau + node * (int64_t)n;
+  const T* Tg = a.Tw + node * nn;
   const int mode = a.mode;
+  const bool trans = mode == kApplyQT;
   auto slot_ptr = [&](int b) -> T* { return a.C + (c0 + b) * a.slot_stride + k0 * a.ldc; };
-  auto sl = [&](int b, int c, int i) -> T& { return Sl[((size_t)b * kcw + c) * ldn + i]; };
-
-  for (int b = 0; b < nc; ++b) {
-    const T* src = slot_ptr(b);
-    const bool zero = mode == kApplyForm && b > 0;
-    for (int idx = tid; idx < n * kcw; idx += NT) {
-      const int i = idx % n, c = idx / n;
-      sl(b, c, i) = (!zero && c < kc) ? src[i + (int64_t)c * a.ldc] : T(0);
-    }
-  }
-  for (int b = 1; b < nc; ++b)
+  auto load_y = [&](int b) {
+    const T* Yb = Yn + (int64_t)(b - 1) * nn;
     for (int idx = tid; idx < n * n; idx += NT) {
       const int i = idx % n, p = idx / n;
-      Ys[((size_t)(b - 1) * n + p) * ldn + i] = i <= p ? Yn[(int64_t)(b - 1) * nn + idx] : T(0);
+      Ys[p * ldn + i] = Yb[idx];
     }
-  __syncthreads();
-  const int G = NT / kcw;               // row groups per column
-  const int c = tid % kcw, g = tid / kcw;
-  for (int s = 0; s < n; ++s) {
-    const int j = mode == kApplyQT ? s : n - 1 - s;
-    const T tj = taun[j];
-    if (tj == T(0)) continue;  // H_j = I (uniform across the block)
-    const int jr = j + 1;
-    const int vrows = 1 + (nc - 1) * jr;
-    const int chunk = (vrows + G - 1) / G;
-    int v = g * chunk;
-    const int v1 = min(v + chunk, vrows);
-    // Partial dot u_j^T C(:, c) over this thread's virtual rows.
-    T acc = T(0);
-    {
-      int vv = v;
-      if (vv == 0 && vv < v1) {
-        acc = sl(0, c, j);
-        ++vv;
-      }
-      if (vv < v1) {
-        int b = 1 + (vv - 1) / jr, i = (vv - 1) % jr;
-        for (; vv < v1; ++vv) {
-          acc = fma(Ys[((size_t)(b - 1) * n + j) * ldn + i], sl(b, c, i), acc);
-          if (++i == jr) {
-            i = 0;
-            ++b;
-          }
-        }
-      }
+  };
+
+  for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
+  {  // W = C_0 (form: X)
+    const T* src = slot_ptr(0);
+    for (int idx = tid; idx < n * kc; idx += NT) {
+      const int i = idx % n, c = idx / n;
+      B2[c * ldn + i] = src[i + (int64_t)c * a.ldc];
     }
-    part[g * kcw + c] = acc;
-    __syncthreads();
-    T w = T(0);
-    for (int gg = 0; gg < G; ++gg) w += part[gg * kcw + c];
-    const T coef = tj * w;
-    if (v == 0 && v < v1) {
-      sl(0, c, j) -= coef;
-      ++v;
-    }
-    if (v < v1) {
-      int b = 1 + (v - 1) / jr, i = (v - 1) % jr;
-      for (; v < v1; ++v) {
-        sl(b, c, i) -= coef * Ys[((size_t)(b - 1) * n + j) * ldn + i];
-        if (++i == jr) {
-          i = 0;
-          ++b;
-        }
-      }
-    }
-    __syncthreads();
   }
-  for (int b = 0; b < nc; ++b) {
+  constexpr int PG = NT / KC;
+  const int cc = tid % KC, pg = tid / KC;
+  if (mode != kApplyForm) {
+    // W += Y_b^T C_b; Y_b is upper triangular, so W(p) sums rows i <= p.
+    for (int b = 1; b < nc; ++b) {
+      __syncthreads();
+      const T* src = slot_ptr(b);
+      for (int idx = tid; idx < n * kc; idx += NT) {
+        const int i = idx % n, c = idx / n;
+        B1[c * ldn + i] = src[i + (int64_t)c * a.ldc];
+      }
+      load_y(b);
+      __syncthreads();
+      if (cc < kc) {
+        for (int p = pg; p < n; p += PG) {
+          T s = B2[cc * ldn + p];
+          for (int i = 0; i <= p; ++i) s = fma(Ys[p * ldn + i], B1[cc * ldn + i], s);
+          B2[cc * ldn + p] = s;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // W' = T^T W (Q^T) or T W (Q, form), into B1.
+  if (cc < kc) {
+    for (int p = pg; p < n; p += PG) {
+      T s = T(0);
+      if (trans) {
+        for (int qq = 0; qq <= p; ++qq) s = fma(Ts[qq + p * n], B2[cc * ldn + qq], s);
+      } else {
+        for (int qq = p; qq < n; ++qq) s = fma(Ts[p + qq * n], B2[cc * ldn + qq], s);
+      }
+      B1[cc * ldn + p] = s;
+    }
+  }
+  __syncthreads();
+  {  // C_0 <- C_0 - W'  (form: X - W')
+    T* dst = slot_ptr(0);
+    for (int idx = tid; idx < n * kc; idx += NT) {
+      const int i = idx % n, c = idx / n;
+      dst[i + (int64_t)c * a.ldc] -= B1[c * ldn + i];
+    }
+  }
+  // C_b <- C_b - Y_b W'  (form: -Y_b W').
+  for (int b = 1; b < nc; ++b) {
+    __syncthreads();
+    load_y(b);
+    __syncthreads();
+    if (cc < kc) {
+      for (int i = pg; i < n; i += PG) {
+        T s = T(0);
+        for (int p = i; p < n; ++p) s = fma(Ys[p * ldn + i], B1[cc * ldn + p], s);
+        B2[cc * ldn + i] = s;
+      }
+    }
+    __syncthreads();
     T* dst = slot_ptr(b);
     for (int idx = tid; idx < n * kc; idx += NT) {
-      const int i = idx % n, cc = idx / n;
-      dst[i + (int64_t)cc * a.ldc] = sl(b, cc, i);
+      const int i = idx % n, c = idx / n;
+      T* e = dst + i + (int64_t)c * a.ldc;
+      *e = (mode == kApplyForm ? T(0) : *e) - B2[c * ldn + i];
     }
   }
 }
@@ -328,21 +329,10 @@ size_t leaf_apply_smem(int n, size_t elem) {
          elem * (size_t)n * kApplyCols + elem * (size_t)n * n;
 }
 
-// Shared memory of the node apply kernel for slices of kcw columns.
-size_t node_apply_smem_kc(int n, int q, size_t elem, int kcw) {
-  const int ldn = n | 1;
-  return elem * ((size_t)q * kcw * ldn + (size_t)(q - 1) * n * ldn + kApplyThreads);
-}
-
-// Widest column slice (64, 32 or 16) whose node apply fits in max_bytes; 0 if none.
-int node_apply_kc(int n, int q, size_t elem, size_t max_bytes) {
-  for (int kcw = kApplyCols; kcw >= 16; kcw /= 2)
-    if (node_apply_smem_kc(n, q, elem, kcw) <= max_bytes) return kcw;
-  return 0;
-}
-
 size_t node_apply_smem(int n, int q, size_t elem) {
-  return node_apply_smem_kc(n, q, elem, 16);
+  (void)q;
+  const int ldn = n | 1;
+  return elem * ((size_t)2 * kApplyCols * ldn + (size_t)n * ldn + (size_t)n * n);
 }
 
 template <typename T>
@@ -360,19 +350,13 @@ cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_node_apply(const NodeApplyArgs<T>& a0, cudaStream_t s) {
-  if (a0.nodes <= 0 || a0.k <= 0 || a0.n <= 0) return cudaSuccess;
-  int dev = 0, smax = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  NodeApplyArgs<T> a = a0;
-  a.kc_chunk = node_apply_kc(a.n, a.arity, sizeof(T), (size_t)smax);
-  if (a.kc_chunk == 0) return cudaErrorInvalidConfiguration;
-  const size_t smem = node_apply_smem_kc(a.n, a.arity, sizeof(T), a.kc_chunk);
+cudaError_t launch_node_apply(const NodeApplyArgs<T>& a, cudaStream_t s) {
+  if (a.nodes <= 0 || a.k <= 0 || a.n <= 0) return cudaSuccess;
+  const size_t smem = node_apply_smem(a.n, a.arity, sizeof(T));
   auto kern = node_apply_kernel<T, kApplyThreads>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t kchunks = (a.k + a.kc_chunk - 1) / a.kc_chunk;
+  const int64_t kchunks = (a.k + kApplyCols - 1) / kApplyCols;
   if (kchunks > 65535 || a.nodes > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)a.nodes, (unsigned)kchunks);
   kern<<<grid, kApplyThreads, smem, s>>>(a);

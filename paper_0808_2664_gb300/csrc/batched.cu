@@ -141,8 +141,9 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchArgs<T> a) {
       }
       __syncthreads();
       if (sh_ok) {
-        node_factor_one<T, NT>(Rin + c0 * nn, nc, M.q, n, L.R + w.idx * nn, L.Y + w.idx * (int64_t)(M.q - 1) * nn,
-                               L.tau + w.idx * (int64_t)n, a.status, smem);
+        node_factor_one<T, NT, false>(Rin + c0 * nn, nc, M.q, n, L.R + w.idx * nn,
+                                      L.Y + w.idx * (int64_t)(M.q - 1) * nn, nullptr, L.tau + w.idx * (int64_t)n,
+                                      a.status, smem);
       }
       done_r = L.R + w.idx * nn;
     }

@@ -104,10 +104,12 @@ extern "C" int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t ld
   const size_t nn = (size_t)n * n * 8, nv = (size_t)n * 8;
   size_t off_leafR = 0, off_leafT = al(nl * nn), off_leafTau = off_leafT + al(nl * nn);
   size_t off = off_leafTau + al(nl * nv);
-  size_t offR[kMaxLevels], offY[kMaxLevels], offTau[kMaxLevels];
+  size_t offR[kMaxLevels], offT[kMaxLevels], offY[kMaxLevels], offTau[kMaxLevels];
   for (int l = 1; l <= levels; ++l) {
     const size_t it = (size_t)items[l];
     offR[l - 1] = off;
+    off += al(it * nn);
+    offT[l - 1] = off;
     off += al(it * nn);
     offY[l - 1] = off;
     off += al(it * (q - 1) * nn);
@@ -149,6 +151,7 @@ extern "C" int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t ld
     na.Rout = (double*)(b + offR[l - 1]);
     na.Y = (double*)(b + offY[l - 1]);
     na.tau = (double*)(b + offTau[l - 1]);
+    na.Tw = (double*)(b + offT[l - 1]);
     na.status = status;
     if (launch_node_factor(na, s) != cudaSuccess) return TSQR_ERR_CUDA;
   }

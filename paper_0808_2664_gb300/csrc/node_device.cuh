@@ -27,12 +27,13 @@ __host__ __device__ inline size_t node_smem_bytes(int n, int q, size_t elem, int
 // Factors one node: the nc upper-triangular n x n children stored
 // contiguously from Rin (ld n each; read with L1-bypassing loads so that a
 // child written by another CTA of the same launch is seen), arity q.  Writes
-// the node's R (Ro), its q-1 upper-triangular reflector blocks (Yo) and tau
-// (tauo).  Node reflectors are applied one by one (no compact-WY T): for the
-// structured Y of a node that costs fewer flops than the WY form.  A lone child (nc = 1) passes through with
+// the node's R (Ro), its q-1 upper-triangular reflector blocks (Yo), tau
+// (tauo) and, when kBuildT, the compact-WY T (To): Z = strictly-upper(Y^T Y)
+// summed over the lower blocks using their triangular structure (n^3/6 for
+// q = 2), then the doubling merges.  A lone child (nc = 1) passes through with
 // an identity Q.  Every thread of the block calls it.
-template <typename T, int NT>
-__device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo, T* tauo, int* status,
+template <typename T, int NT, bool kBuildT>
+__device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo, T* To, T* tauo, int* status,
                                 unsigned char* smem) {
   const int ld = node_ld(n);
   T* S = reinterpret_cast<T*>(smem);
@@ -47,6 +48,7 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
     // A lone child passes up unchanged: its Q factor is the identity.
     for (int64_t idx = tid; idx < nn; idx += NT) {
       Ro[idx] = __ldcg(Rin + idx);
+      if (kBuildT) To[idx] = T(0);
     }
     for (int64_t idx = tid; idx < (int64_t)(q - 1) * nn; idx += NT) Yo[idx] = T(0);
     for (int c = tid; c < n; c += NT) tauo[c] = T(0);
@@ -173,6 +175,35 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
   }
   for (int c = tid; c < n; c += NT) tauo[c] = (T)tau_s[c];
   __syncthreads();
+  if (kBuildT) {
+    // T lives in block 0's region (R already written out); the doubling
+    // workspace reuses block 1's region once Z no longer needs Y.
+    T* Tm = S;
+    T* Wt = S + (size_t)n * ld;
+    for (int64_t idx = tid; idx < nn; idx += NT) {  // diagonal and below; Z fills above
+      const int p = (int)(idx % n), jj = (int)(idx / n);
+      if (p >= jj) Tm[idx] = p == jj ? (T)tau_s[p] : T(0);
+    }
+    // Pairs (p, j), p < j, p-major: the lanes of a warp share p, so every
+    // lane runs the same (nc - 1)(p + 1)-term sum.
+    const int npairs = n * (n - 1) / 2;
+    for (int idx = tid; idx < npairs; idx += NT) {
+      int p = 0, rem = idx;
+      while (rem >= n - 1 - p) {
+        rem -= n - 1 - p;
+        ++p;
+      }
+      const int jj = p + 1 + rem;
+      T z = T(0);
+      for (int b = 1; b < nc; ++b)
+        for (int i = 0; i <= p; ++i) z = fma(at(b, p, i), at(b, jj, i), z);
+      Tm[p + (int64_t)jj * n] = z;
+    }
+    __syncthreads();
+    build_t_doubling(Tm, Wt, n);
+    for (int64_t idx = tid; idx < nn; idx += NT) To[idx] = Tm[idx];
+    __syncthreads();
+  }
 }
 
 }  // namespace tsqr

@@ -28,8 +28,9 @@ __global__ void __launch_bounds__(NT) node_factor_kernel(NodeFactorArgs<T> a) {
   for (int64_t node = blockIdx.x; node < a.nodes; node += gridDim.x) {
     const int64_t c0 = node * q;
     const int nc = (int)((a.nin - c0) < q ? (a.nin - c0) : q);
-    node_factor_one<T, NT>(a.Rin + c0 * nn, nc, q, n, a.Rout + node * nn, a.Y + node * (int64_t)(q - 1) * nn,
-                           a.tau + node * (int64_t)n, a.status, smem);
+    node_factor_one<T, NT, true>(a.Rin + c0 * nn, nc, q, n, a.Rout + node * nn,
+                                 a.Y + node * (int64_t)(q - 1) * nn, a.Tw + node * nn, a.tau + node * (int64_t)n,
+                                 a.status, smem);
   }
 }
 

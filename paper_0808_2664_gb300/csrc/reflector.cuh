@@ -112,10 +112,11 @@ __device__ __forceinline__ void build_t_doubling(T* Tm, T* Wt, int n) {
       Wt[pair * bb + pl + ql * b] = acc;
     }
     __syncthreads();
-    // Pass 2: T12 = -T1 W.
+    // Pass 2: T12 = -T1 W; the lanes of a warp share p, so their sums have
+    // the same length.
     for (int idx = threadIdx.x; idx < npairs * bb; idx += blockDim.x) {
       const int pair = idx / bb, rem = idx % bb;
-      const int pl = rem % b, ql = rem / b;
+      const int ql = rem % b, pl = rem / b;
       const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
       if (q >= n) continue;
       T acc = T(0);

@@ -59,6 +59,7 @@ struct NodeFactorArgs {
   T* Rout;          // nodes x (n x n)
   T* Y;             // nodes x (q-1) x (n x n): upper-triangular reflector blocks
   T* tau;           // nodes x n
+  T* Tw;            // nodes x (n x n): compact-WY T
   int* status;
 };
 
@@ -80,7 +81,7 @@ struct LeafApplyArgs {
 template <typename T>
 struct NodeApplyArgs {
   const T* Y;       // nodes x (q-1) x (n x n)
-  const T* tau;     // nodes x n
+  const T* Tw;      // nodes x (n x n)
   int64_t nin;      // items of the level below
   int arity;
   int n;
@@ -90,7 +91,6 @@ struct NodeApplyArgs {
   int64_t ldc;
   int64_t k;
   int mode;
-  int kc_chunk;     // columns of C per CTA (set by the launcher)
 };
 
 template <typename T>
