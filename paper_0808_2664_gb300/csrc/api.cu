@@ -145,22 +145,32 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
   const int64_t smax = max_smem_optin();
   int64_t h = opts && opts->leaf_rows > 0 ? opts->leaf_rows : 0;
   if (h == 0) {
-    // Largest power of two (at most 1024) whose n-column leaf tile stays
-    // within about 68 KB, so that three leaf CTAs share an SM and hide each
-    // other's serial reflector steps.
-    const int64_t budget = 68 * 1024 / (int64_t)q->es;
-    h = 1;
-    while (h * 2 <= budget / n && h * 2 <= 1024) h *= 2;
+    // Tallest leaf (a multiple of 32 rows, at most 1024) whose n-column tile
+    // fits in about 200 KB of shared memory: taller leaves mean fewer tree
+    // nodes (the tree's work is about n / (2h) of the leaves') and a smaller
+    // n^3 share in forming Q, at one leaf CTA per SM.
+    const int64_t budget = 200 * 1024 / (int64_t)q->es;
+    h = budget / n / 32 * 32;
+    if (h > 1024) h = 1024;
     if (h < n) h = n;
   }
   if (h < n) return -4;
-  int64_t nl = (m + h - 1) / h;
-  if (nl < 1) nl = 1;
-  const int64_t rem = m - (nl - 1) * h;
-  if (nl > 1 && rem < n) --nl;
+  const bool auto_h = !(opts && opts->leaf_rows > 0);
+  int64_t nl = 0;
+  for (;;) {
+    nl = (m + h - 1) / h;
+    if (nl < 1) nl = 1;
+    const int64_t rem = m - (nl - 1) * h;
+    if (nl > 1 && rem < n) --nl;
+    q->hmax = nl > 1 ? (m - (nl - 1) * h > h ? m - (nl - 1) * h : h) : m;
+    // An automatic height shrinks until a merged last leaf still fits.
+    if (!auto_h || h - 32 < n ||
+        (int64_t)leaf_factor_smem((int)n, leaf_factor_ld((int)q->hmax), q->es) <= smax)
+      break;
+    h -= 32;
+  }
   q->h = h;
   q->nleaves = nl;
-  q->hmax = nl > 1 ? (m - (nl - 1) * h > h ? m - (nl - 1) * h : h) : m;
   q->q = opts && opts->arity > 0 ? opts->arity : 2;
   if (q->q < 2 || q->q > 16) return -4;
   q->items.assign(1, nl);

@@ -44,14 +44,21 @@ __global__ void __launch_bounds__(NT) leaf_factor_kernel(LeafFactorArgs<T> a) {
 
 int leaf_factor_ld(int hmax) { return hmax | 1; }
 
-size_t leaf_factor_smem(int n, int hmax, size_t elem) {
-  return leaf_smem_bytes(n, leaf_factor_ld(hmax), elem, elem == 8 ? kLeafThreads64 : kLeafThreads32);
+// Threads per leaf CTA: FP64 leaves use 128 when three tiles share an SM and
+// 256 when a tile is so tall that only one CTA fits; FP32 leaves use 256.
+int leaf_factor_threads(int n, int ld, size_t elem) {
+  if (leaf_tile_region(n, ld, elem) > 100 * 1024) return kLeafThreadsBig;
+  return elem == 4 ? kLeafThreads32 : kLeafThreads64;
 }
-template <typename T>
-cudaError_t launch_leaf_factor(const LeafFactorArgs<T>& a, cudaStream_t s) {
-  if (a.nleaves <= 0 || a.n <= 0) return cudaSuccess;
-  constexpr int NT = sizeof(T) == 8 ? kLeafThreads64 : kLeafThreads32;
-  const size_t smem = leaf_factor_smem(a.n, a.ld_s, sizeof(T));
+
+size_t leaf_factor_smem(int n, int hmax, size_t elem) {
+  const int ld = leaf_factor_ld(hmax);
+  return leaf_smem_bytes(n, ld, elem, leaf_factor_threads(n, ld, elem));
+}
+
+template <typename T, int NT>
+cudaError_t launch_leaf_factor_nt(const LeafFactorArgs<T>& a, cudaStream_t s) {
+  const size_t smem = leaf_smem_bytes(a.n, a.ld_s, sizeof(T), NT);
   auto kern = a.n <= 64 ? leaf_factor_kernel<T, NT, 64> : leaf_factor_kernel<T, NT, kMaxN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -64,6 +71,14 @@ cudaError_t launch_leaf_factor(const LeafFactorArgs<T>& a, cudaStream_t s) {
   if (grid > a.nleaves) grid = a.nleaves;
   kern<<<(unsigned)grid, NT, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_leaf_factor(const LeafFactorArgs<T>& a, cudaStream_t s) {
+  if (a.nleaves <= 0 || a.n <= 0) return cudaSuccess;
+  const int nt = leaf_factor_threads(a.n, a.ld_s, sizeof(T));
+  if (nt == kLeafThreadsBig) return launch_leaf_factor_nt<T, kLeafThreadsBig>(a, s);
+  return nt == 256 ? launch_leaf_factor_nt<T, 256>(a, s) : launch_leaf_factor_nt<T, 128>(a, s);
 }
 
 template cudaError_t launch_leaf_factor<double>(const LeafFactorArgs<double>&, cudaStream_t);

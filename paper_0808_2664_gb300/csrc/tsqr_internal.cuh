@@ -14,6 +14,7 @@ constexpr int kStatusTimeout = 2;
 // Threads per CTA of the factor and apply kernels.
 constexpr int kLeafThreads64 = 128;  // FP64 leaves
 constexpr int kLeafThreads32 = 256;  // FP32-storage leaves
+constexpr int kLeafThreadsBig = 512; // leaves whose tile leaves room for one CTA per SM
 constexpr int kNodeThreads = 128;
 constexpr int kApplyThreads = 256;
 // Columns of C handled by one CTA of the apply kernels.
