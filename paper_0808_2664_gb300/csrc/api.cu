@@ -149,9 +149,15 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     // fits in about 200 KB of shared memory: taller leaves mean fewer tree
     // nodes (the tree's work is about n / (2h) of the leaves') and a smaller
     // n^3 share in forming Q, at one leaf CTA per SM.
-    const int64_t budget = 200 * 1024 / (int64_t)q->es;
-    h = budget / n / 32 * 32;
-    if (h > 1024) h = 1024;
+    // FP32 leaves are cheap in arithmetic and latency-bound, so they keep
+    // 68 KB tiles (three 256-thread CTAs per SM) instead.
+    if (q->es == 8) {
+      h = 200 * 1024 / 8 / n / 32 * 32;
+      if (h > 1024) h = 1024;
+    } else {
+      h = 1;
+      while (h * 2 <= 68 * 1024 / 4 / n && h * 2 <= 1024) h *= 2;
+    }
     if (h < n) h = n;
   }
   if (h < n) return -4;
