@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kUN = 128;       // columns of C per CTA (MMA M of step 1, N of step 3)
 constexpr int kUChunk = 64;    // leaf rows staged per step-1 chunk
-constexpr int kUThreads = 128; // four warps: one TMEM lane quarter each
+constexpr int kUThreads = 256; // eight warps; warps w and w+4 share TMEM lane quarter w % 4
 constexpr int kUNp = 64;       // reflector count padded to the MMA N / K granularity
 constexpr int kTmemCols = 256; // D1 at columns [0, 64), D2 at [64, 192)
 constexpr long long kPollLimit = 1ll << 24;
@@ -114,26 +114,44 @@ struct Bf16x3Args {
   int64_t ldc;
   int64_t k;
   int* status;
+  int vec;  // 16-byte loads allowed (C, Y, ldc, ldy, h aligned)
 };
 
-// Shared memory map (bytes from a 1024-aligned base).
-constexpr uint32_t kOffA1 = 0;                         // C^T chunk hi | lo: 2 x 128x64 bf16
-constexpr uint32_t kSzA1 = kUN * kUChunk * 2;          // 16 KB per term
-constexpr uint32_t kOffB1 = kOffA1 + 2 * kSzA1;        // Y chunk hi | lo: 2 x 64x64 bf16
-constexpr uint32_t kSzB1 = kUNp * kUChunk * 2;         // 8 KB per term
-constexpr uint32_t kOffA3 = kOffB1 + 2 * kSzB1;        // Y row tile hi | lo: 2 x 128x64 bf16
-constexpr uint32_t kSzA3 = 128 * kUNp * 2;             // 16 KB per term
-constexpr uint32_t kOffB3 = kOffA3 + 2 * kSzA3;        // W' hi | lo: 2 x 128x64 bf16
-constexpr uint32_t kSzB3 = kUN * kUNp * 2;             // 16 KB per term
+// Shared memory map (bytes from a 1024-aligned base).  Step 1's operand
+// tiles are double-buffered so the next chunk is staged while the tensor
+// cores work on the current one.
+constexpr uint32_t kSzA1 = kUN * kUChunk * 2;          // C^T chunk, one BF16 term: 16 KB
+constexpr uint32_t kSzB1 = kUNp * kUChunk * 2;         // Y chunk, one term: 8 KB
+constexpr uint32_t kOffA1 = 0;                         // [buffer][hi | lo]
+constexpr uint32_t kOffB1 = kOffA1 + 4 * kSzA1;        // [buffer][hi | lo]
+constexpr uint32_t kSzA3 = 128 * kUNp * 2;             // Y row tile, one term: 16 KB
+constexpr uint32_t kOffA3 = kOffB1 + 4 * kSzB1;
+constexpr uint32_t kSzB3 = kUN * kUNp * 2;             // W', one term: 16 KB
+constexpr uint32_t kOffB3 = kOffA3 + 2 * kSzA3;
 constexpr uint32_t kOffT = kOffB3 + 2 * kSzB3;         // T: 64x64 fp32
 constexpr uint32_t kOffBar = kOffT + kUNp * kUNp * 4;  // mbarrier (8 B) + tmem address (4 B)
 constexpr uint32_t kSmemBytes = kOffBar + 64 + 1024;   // + alignment slack
+
+// Four consecutive BF16 hi (and lo) terms of x[0..3] at byte offset off (8-byte aligned).
+__device__ __forceinline__ void split_store4(unsigned char* hi_base, unsigned char* lo_base, uint32_t off,
+                                             const float* x) {
+  __nv_bfloat16 h[4], l[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    h[e] = __float2bfloat16_rn(x[e]);
+    l[e] = __float2bfloat16_rn(x[e] - __bfloat162float(h[e]));
+  }
+  *reinterpret_cast<uint2*>(hi_base + off) = *reinterpret_cast<const uint2*>(h);
+  *reinterpret_cast<uint2*>(lo_base + off) = *reinterpret_cast<const uint2*>(l);
+}
 
 __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
+  const int quarter = (tid >> 5) & 3;  // TMEM lane quarter this warp may access
+  const int half = tid >> 7;           // 0: threads 0..127, 1: threads 128..255
   const int n = a.n;
   const int64_t leaf = blockIdx.x;
   const int64_t k0 = (int64_t)blockIdx.y * kUN;
@@ -150,7 +168,7 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + kOffBar + 8),
                  "r"(kTmemCols)
                  : "memory");
@@ -167,73 +185,117 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t d1 = tmem, d2 = tmem + kUNp;
-  uint32_t phase = 0;
+  uint32_t commits = 0, waited = 0;  // tcgen05.commit k completes mbarrier phase k
   bool ok = true;
-
-  auto yval = [&](int row, int p) -> float {
-    if (p >= n || row >= hl || row < p) return 0.f;
-    return row == p ? 1.f : Yg[row + (int64_t)p * a.ldy];
-  };
-
-  // ---- Step 1: W^T = C^T Y over the leaf rows, 64 rows per chunk.
-  const int nchunks = (hl + kUChunk - 1) / kUChunk;
-  for (int ch = 0; ch < nchunks && ok; ++ch) {
-    const int rb = ch * kUChunk;
-    for (int idx = tid; idx < kUN * kUChunk; idx += kUThreads) {
-      const int kk = idx % kUChunk, c = idx / kUChunk;  // consecutive threads walk rows (coalesced)
-      const int row = rb + kk;
-      const float x = (row < hl && c < kc) ? Cg[row + (int64_t)c * a.ldc] : 0.f;
-      split_store(sm + kOffA1, sm + kOffA1 + kSzA1, kmaj(c, kk, kUN), x);
+  auto wait_next = [&]() {
+    if (mbar_wait(mbar, waited & 1)) {
+      ++waited;
+    } else {
+      ok = false;
+      if (tid == 0) atomicOr(a.status, kStatusTimeout);
     }
-    for (int idx = tid; idx < kUNp * kUChunk; idx += kUThreads) {
-      const int kk = idx % kUChunk, p = idx / kUChunk;
-      split_store(sm + kOffB1, sm + kOffB1 + kSzB1, kmaj(p, kk, kUNp), yval(rb + kk, p));
+  };
+  // Four rows r..r+3 of column col of a column-major FP32 matrix (rows
+  // beyond hl are zero): one 16-byte load when aligned and complete.
+  auto load4 = [&](const float* base, int64_t ld, int r, int col, float* x) {
+    const float* p = base + r + (int64_t)col * ld;
+    if (a.vec && r + 3 < hl) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+      x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x[e] = (r + e < hl) ? p[e] : 0.f;
+    }
+  };
+  auto mask_y = [&](int r, int p, float* x) {  // unit diagonal, zero above, padding beyond n
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int row = r + e;
+      if (p >= n || row >= hl || row < p) x[e] = 0.f;
+      else if (row == p) x[e] = 1.f;
+    }
+  };
+  auto stage1 = [&](int ch, int buf) {
+    const int rb = ch * kUChunk;
+    unsigned char* ahi = sm + kOffA1 + (2 * buf) * kSzA1;
+    unsigned char* bhi = sm + kOffB1 + (2 * buf) * kSzB1;
+    for (int idx = tid; idx < kUN * (kUChunk / 4); idx += kUThreads) {
+      const int quad = idx % (kUChunk / 4), c = idx / (kUChunk / 4);
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (c < kc) load4(Cg, a.ldc, rb + 4 * quad, c, x);
+      split_store4(ahi, ahi + kSzA1, kmaj(c, 4 * quad, kUN), x);
+    }
+    for (int idx = tid; idx < kUNp * (kUChunk / 4); idx += kUThreads) {
+      const int quad = idx % (kUChunk / 4), p = idx / (kUChunk / 4);
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (p < n) load4(Yg, a.ldy, rb + 4 * quad, p, x);
+      mask_y(rb + 4 * quad, p, x);
+      split_store4(bhi, bhi + kSzB1, kmaj(p, 4 * quad, kUNp), x);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+  };
+  auto issue1 = [&](int ch, int buf) {
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       constexpr uint32_t id1 = idesc_bf16(kUN, kUNp);
+      const uint32_t A = sbase + kOffA1 + (2 * buf) * kSzA1, B = sbase + kOffB1 + (2 * buf) * kSzB1;
 #pragma unroll
       for (int s = 0; s < kUChunk / 16; ++s) {
         const uint32_t aoff = (uint32_t)s * kUN * 32, boff = (uint32_t)s * kUNp * 32;
-        const uint64_t ahi = sdesc(sbase + kOffA1 + aoff, kUN * 16, 128);
-        const uint64_t alo = sdesc(sbase + kOffA1 + kSzA1 + aoff, kUN * 16, 128);
-        const uint64_t bhi = sdesc(sbase + kOffB1 + boff, kUNp * 16, 128);
-        const uint64_t blo = sdesc(sbase + kOffB1 + kSzB1 + boff, kUNp * 16, 128);
+        const uint64_t ahi = sdesc(A + aoff, kUN * 16, 128), alo = sdesc(A + kSzA1 + aoff, kUN * 16, 128);
+        const uint64_t bhi = sdesc(B + boff, kUNp * 16, 128), blo = sdesc(B + kSzB1 + boff, kUNp * 16, 128);
         mma_bf16(d1, ahi, bhi, id1, (ch > 0 || s > 0) ? 1u : 0u);
         mma_bf16(d1, ahi, blo, id1, 1u);
         mma_bf16(d1, alo, bhi, id1, 1u);
       }
       mma_commit(mbar);
     }
-    if (mbar_wait(mbar, phase & 1)) {
-      ++phase;
-    } else {
-      ok = false;
-      if (tid == 0) atomicOr(a.status, kStatusTimeout);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-  }
+    ++commits;
+  };
 
-  // ---- Step 2: W'^T(c, :) = W^T(c, :) T, thread c = TMEM lane c.
+  // ---- Step 1: W^T = C^T Y over the leaf rows, 64 rows per chunk; chunk
+  // ch+1 is staged while the MMAs of chunk ch run.
+  const int nchunks = (hl + kUChunk - 1) / kUChunk;
+  stage1(0, 0);
+  __syncthreads();
+  issue1(0, 0);
+  for (int ch = 1; ch < nchunks && ok; ++ch) {
+    stage1(ch, ch & 1);  // buffer ch&1 was read by chunk ch-2, already complete
+    __syncthreads();
+    wait_next();  // chunk ch-1 done
+    if (!ok) break;
+    issue1(ch, ch & 1);
+  }
+  if (ok) wait_next();  // last chunk done
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+
+  // ---- Step 2: W'^T(c, :) = W^T(c, :) T.  Thread (half, c): column c of C,
+  // W' columns q in [32 half, 32 half + 32).
   if (ok) {
+    const int c = tid & (kUN - 1);
     float w[kUNp];
 #pragma unroll
-    for (int q = 0; q < kUNp; q += 16) tmem_ld16(d1 + ((uint32_t)(warp * 32) << 16) + q, w + q);
-    const int c = tid;
-    float wp[kUNp];
+    for (int q = 0; q < kUNp; q += 16) tmem_ld16(d1 + ((uint32_t)(quarter * 32) << 16) + q, w + q);
+    float wp[32];
 #pragma unroll
-    for (int q = 0; q < kUNp; ++q) wp[q] = 0.f;
-    // T is upper triangular: W'^T(c, q) = sum_{p <= q} W^T(c, p) T(p, q).
+    for (int q = 0; q < 32; ++q) wp[q] = 0.f;
+    if (half == 0) {
 #pragma unroll
-    for (int p = 0; p < kUNp; ++p) {
+      for (int p = 0; p < 32; ++p)
 #pragma unroll
-      for (int q = p; q < kUNp; ++q) wp[q] = fmaf(w[p], Ts[p + q * kUNp], wp[q]);
+        for (int q = p; q < 32; ++q) wp[q] = fmaf(w[p], Ts[p + q * kUNp], wp[q]);
+    } else {
+#pragma unroll
+      for (int p = 0; p < kUNp; ++p)
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (p <= q + 32) wp[q] = fmaf(w[p], Ts[p + (q + 32) * kUNp], wp[q]);
     }
 #pragma unroll
-    for (int q = 0; q < kUNp; ++q) split_store(sm + kOffB3, sm + kOffB3 + kSzB3, kmaj(c, q, kUN), wp[q]);
+    for (int q = 0; q < 32; q += 4)
+      split_store4(sm + kOffB3, sm + kOffB3 + kSzB3, kmaj(c, 32 * half + q, kUN), wp + q);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -242,9 +304,13 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
   const int ntiles = (hl + 127) / 128;
   for (int t = 0; t < ntiles && ok; ++t) {
     const int rt = t * 128;
-    for (int idx = tid; idx < 128 * kUNp; idx += kUThreads) {
-      const int rr = idx % 128, p = idx / 128;
-      split_store(sm + kOffA3, sm + kOffA3 + kSzA3, kmaj(rr, p, 128), yval(rt + rr, p));
+    for (int idx = tid; idx < 32 * kUNp; idx += kUThreads) {
+      const int quad = idx % 32, p = idx / 32;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (p < n) load4(Yg, a.ldy, rt + 4 * quad, p, x);
+      mask_y(rt + 4 * quad, p, x);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) split_store(sm + kOffA3, sm + kOffA3 + kSzA3, kmaj(4 * quad + e, p, 128), x[e]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -264,19 +330,15 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
       }
       mma_commit(mbar);
     }
-    if (mbar_wait(mbar, phase & 1)) {
-      ++phase;
-    } else {
-      ok = false;
-      if (tid == 0) atomicOr(a.status, kStatusTimeout);
-    }
+    ++commits;
+    wait_next();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-      const int row = rt + tid;  // TMEM lane = row of this tile
+      const int row = rt + (tid & 127);  // TMEM lane = row of this tile
 #pragma unroll 1
-      for (int c0 = 0; c0 < kUN; c0 += 16) {
+      for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
         float d[16];
-        tmem_ld16(d2 + ((uint32_t)(warp * 32) << 16) + c0, d);
+        tmem_ld16(d2 + ((uint32_t)(quarter * 32) << 16) + c0, d);
         if (row < hl) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
@@ -289,14 +351,13 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
   }
-  (void)lane;
-  if (!ok) {
-    // The pending commit's phase never completed in time: give the in-flight
-    // MMAs one more bounded wait before tensor memory is released.
-    mbar_wait(mbar, phase & 1);
+  if (!ok && waited < commits) {
+    // A commit's phase did not complete in time: give the in-flight MMAs one
+    // more bounded wait before tensor memory is released.
+    mbar_wait(mbar, waited & 1);
   }
   __syncthreads();
-  if (warp == 0) {
+  if (tid < 32) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
@@ -319,6 +380,10 @@ cudaError_t launch_leaf_update_bf16x3(const LeafApplyArgs<float>& la, int* statu
   a.ldc = la.ldc;
   a.k = la.k;
   a.status = status;
+  a.vec = ((uintptr_t)la.C % 16 == 0 && (uintptr_t)la.Y % 16 == 0 && la.ldc % 4 == 0 && la.ldy % 4 == 0 &&
+           la.h % 4 == 0)
+              ? 1
+              : 0;
   cudaError_t e = cudaFuncSetAttribute(bf16x3_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
   if (e != cudaSuccess) return e;
   const int64_t kchunks = (la.k + kUN - 1) / kUN;
