@@ -21,110 +21,274 @@ __host__ __device__ inline size_t leaf_tile_region(int n, int ld, size_t elem) {
   return tile > tm ? tile : tm;
 }
 
-// Shared-memory bytes for a leaf of up to ld rows with NT threads.
+// Shared-memory bytes for a leaf of up to ld rows with NT threads: the tile
+// region, NT partial dots, two per-column coefficient vectors, and FP64
+// per-column scalars (tau, reflector scale) plus 32 per-warp partial norms.
 __host__ __device__ inline size_t leaf_smem_bytes(int n, int ld, size_t elem, int nt) {
-  return leaf_tile_region(n, ld, elem) + (elem + sizeof(double)) * (size_t)nt + sizeof(double) * (size_t)n;
+  return leaf_tile_region(n, ld, elem) + leaf_align_up(elem * (size_t)nt, 8) + 2 * leaf_align_up(elem * (size_t)n, 8) +
+         sizeof(double) * (3 * (size_t)n + 32);
+}
+
+// Exponent k of the power of two 2^k that brings the largest magnitude of a
+// column, given as the high 32 bits of its IEEE pattern with the sign
+// cleared, to [1/2, 1), clamped so that 2^k and 2^-k are normal numbers of T.
+// Zero, subnormal and non-finite columns get k = 0 (values kept).
+template <typename T>
+__device__ __forceinline__ int column_exp2(unsigned hi) {
+  constexpr bool kF64 = sizeof(T) == 8;
+  const int e = kF64 ? (int)(hi >> 20) : (int)(hi >> 23);  // biased exponent
+  const int emax = kF64 ? 2047 : 255, bias = kF64 ? 1023 : 127;
+  if (e == 0 || e == emax) return 0;
+  const int k = -(e - bias + 1);
+  const int lo = kF64 ? -1021 : -125, hi_k = kF64 ? 1022 : 126;
+  return k < lo ? lo : (k > hi_k ? hi_k : k);
+}
+
+// 2^k as a T, built from its bit pattern (k within T's normal exponents).
+template <typename T>
+__device__ __forceinline__ T pow2_bits(int k) {
+  if constexpr (sizeof(T) == 8) return __longlong_as_double((long long)(k + 1023) << 52);
+  else return __int_as_float((k + 127) << 23);
 }
 
 // Factors one leaf: rows Ag[0..hl) (column stride lda) of an n-column matrix,
 // in place (Y below the diagonal, R_i on and above); writes the leaf R (n x n,
 // ld n) to Rl, tau to taul and the compact-WY T (n x n) to Tg.  Every thread
 // of the block calls it; smem holds leaf_smem_bytes(n, ld, sizeof(T), NT).
+//
+// Schedule.  Each column is first multiplied by a power of two that brings
+// its largest entry to [1/2, 1): Householder QR commutes exactly with such
+// column scalings (Q is unchanged, R's columns carry the factors), and it
+// keeps every product below in range.  The Householder vector of column k is
+// kept unscaled until the end, u_k = [1; s_k a_k(k+1:)] with the reflector's
+// scale s_k, so its dot products can be taken before s_k is known.  Step k:
+//   P   every trailing column c > k receives H_{k-1} (coefficient tau_{k-1}
+//       w_c, with u_{k-1} = s_{k-1} a_{k-1} below its unit entry) and, fused
+//       with that update, its partial dot with a_k's tail; meanwhile warp 0
+//       alone turns column k's (alpha, ||tail||^2) into (beta, tau_k, s_k);
+//   S1  w_c = a_c(k) + s_k (a_k(k+1:)^T a_c(k+1:)) and tau_k w_c per column;
+//   S2  column k + 1 alone receives H_k (four warps, one per SM
+//       sub-partition) and the squared norm of its tail is summed per warp,
+//       ready for the next step's reflector.
+// Three barriers per column; the bulk of the arithmetic (update and dot) is
+// one pass over the trailing block.
 template <typename T, int NT, int NMAX>
 __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl, T* taul, T* Tg, int* status,
                                 unsigned char* smem) {
+  static_assert(NT >= 128, "the leaf schedule needs at least four warps");
   T* S = reinterpret_cast<T*>(smem);
-  // Products (dots, Y^T Y, T) run in the storage type T; squared norms and
-  // the reflector scalars run in FP64.
-  T* part = reinterpret_cast<T*>(smem + leaf_tile_region(n, ld, sizeof(T)));  // NT partial dots
-  double* nrm_part = reinterpret_cast<double*>(part + NT);                    // scratch (n coefficients)
-  double* tau_s = nrm_part + NT;                                              // n
+  unsigned char* aux = smem + leaf_tile_region(n, ld, sizeof(T));
+  T* part = reinterpret_cast<T*>(aux);  // NT partial dots
+  T* coef = reinterpret_cast<T*>(aux + leaf_align_up(sizeof(T) * NT, 8));  // n: tau_k w_c
+  T* cscl = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(coef) + leaf_align_up(sizeof(T) * n, 8));  // n: tau_k w_c s_k
+  double* tau_s = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(cscl) + leaf_align_up(sizeof(T) * n, 8));
+  double* sc_s = tau_s + n;  // n: reflector scales s_k
+  int* cexp = reinterpret_cast<int*>(sc_s + n);  // n: column scaling exponents (n doubles reserved)
+  double* wsum = sc_s + 2 * n;  // 32 per-warp partial squared norms
   T* Tm = reinterpret_cast<T*>(smem);  // n x n, after write-back
   T* Wt = Tm + (size_t)n * n;          // doubling workspace
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  for (int c = 0; c < n; ++c) {
-    const T* src = Ag + (int64_t)c * lda;
-    for (int i = tid; i < hl; i += NT) S[c * ld + i] = src[i];
-  }
-  __syncthreads();
-  T* coefs = reinterpret_cast<T*>(nrm_part);  // per-column tau * w of the current step
+  constexpr int kWarps = NT / 32;
+  constexpr int kS2Warps = 4;           // warps of the single-column phase S2
+  constexpr int NP = NT - 32;           // threads of phase P (all but warp 0)
 
-  for (int j = 0; j < n; ++j) {
-    T* colj = S + j * ld;
-    // Phase C: reflector for column j by one warp, chosen round-robin so the
-    // serial step does not always load the same SM sub-partition.  The
-    // squared norm of the tail is summed by the whole warp (full lanes).
-    if (warp == (j % (NT / 32))) {
-      double ssq = 0.0;
-      for (int i = j + 1 + lane; i < hl; i += 32) {
-        const double x = (double)colj[i];
-        ssq = fma(x, x, ssq);
+  // Load the tile: each thread walks the column-major elements e = tid + t NT,
+  // several loads in flight.
+  {
+    const int total = hl * n;
+    int c = tid / hl, i = tid - c * hl;
+    const int dc = NT / hl, di = NT - dc * hl;
+    int e = tid;
+    for (; e + 3 * NT < total; e += 4 * NT) {
+      T v[4];
+      int cs[4], is[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cs[u] = c;
+        is[u] = i;
+        v[u] = Ag[(int64_t)c * lda + i];
+        c += dc;
+        i += di;
+        if (i >= hl) {
+          i -= hl;
+          ++c;
+        }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
-      double scale = 0.0;
+      for (int u = 0; u < 4; ++u) S[cs[u] * ld + is[u]] = v[u];
+    }
+    for (; e < total; e += NT) {
+      S[c * ld + i] = Ag[(int64_t)c * lda + i];
+      c += dc;
+      i += di;
+      if (i >= hl) {
+        i -= hl;
+        ++c;
+      }
+    }
+  }
+  __syncthreads();
+  // Largest magnitude of each column (one warp per column, integer maxima).
+  for (int c = warp; c < n; c += kWarps) {
+    const T* col = S + c * ld;
+    unsigned mx = 0u;
+    for (int i = lane; i < hl; i += 32) {
+      const T x = col[i];
+      const unsigned bits = sizeof(T) == 8 ? (unsigned)__double2hiint((double)x) : __float_as_uint((float)x);
+      const unsigned a = bits & 0x7fffffffu;
+      mx = a > mx ? a : mx;
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) cexp[c] = column_exp2<T>(mx);
+  }
+  __syncthreads();
+  // Scale each column by its power of two.
+#pragma unroll 4
+  for (int c = 0; c < n; ++c) {
+    const T f = pow2_bits<T>(cexp[c]);
+    T* col = S + c * ld;
+    for (int i = tid; i < hl; i += NT) col[i] *= f;
+  }
+  __syncthreads();
+  // Squared norm of column 0's tail, per S2 warp.
+  if (warp < kS2Warps) {
+    double ss = 0.0;
+    for (int i = 1 + tid; i < hl; i += 32 * kS2Warps) {
+      const double x = (double)S[i];
+      ss = fma(x, x, ss);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (lane == 0) wsum[warp] = ss;
+  }
+  __syncthreads();
+
+  for (int k = 0; k < n; ++k) {
+    T* colk = S + k * ld;
+    const int acols = n - 1 - k;  // trailing columns k+1 .. n-1
+    if (warp == 0) {
+      // Reflector k (lane 0), from alpha = a_k(k) and the per-warp squared
+      // norms of a_k's tail.  Nothing else reads a_k(k) in this phase.
       if (lane == 0) {
-        const double alpha = (double)colj[j];
-        const int len = hl - j - 1;
+        double ssq = 0.0;
+#pragma unroll
+        for (int w = 0; w < kS2Warps; ++w) ssq += wsum[w];
+        const double alpha = (double)colk[k];
+        const int len = hl - k - 1;
         Reflector r = make_reflector(
-            alpha, ssq, [&]() { return scaled_norm(len, [&](int i) { return (double)colj[j + 1 + i]; }); },
+            alpha, ssq, [&]() { return scaled_norm(len, [&](int i) { return (double)colk[k + 1 + i]; }); },
             status);
-        tau_s[j] = r.tau;
-        scale = r.scale;
-        colj[j] = (T)r.beta;
+        tau_s[k] = r.tau;
+        sc_s[k] = r.scale;
+        colk[k] = (T)r.beta;
       }
-      scale = __shfl_sync(0xffffffffu, scale, 0);
-      for (int i = j + 1 + lane; i < hl; i += 32) colj[i] = (T)((double)colj[i] * scale);
+      __syncwarp();
+    } else if (acols > 0) {
+      // P: H_{k-1} on column c and the partial dot with a_k's tail, rows
+      // interleaved over the rg groups (group g takes rows k-1+g, k-1+g+rg, ...).
+      const int ptid = tid - 32;
+      int rg = NP / acols;
+      {
+        int byrows = (hl - k) / kLeafMinRows;
+        if (byrows < 1) byrows = 1;
+        if (rg > byrows) rg = byrows;
+        if (rg < 1) rg = 1;
+      }
+      const int slot = ptid % acols, g = ptid / acols;
+      const int c = k + 1 + slot;
+      if (g < rg) {
+        T* cc = S + c * ld;
+        T s0 = T(0), s1 = T(0);
+        if (k == 0) {
+          int i = 1 + g;
+          for (; i + rg < hl; i += 2 * rg) {
+            s0 = fma(colk[i], cc[i], s0);
+            s1 = fma(colk[i + rg], cc[i + rg], s1);
+          }
+          if (i < hl) s0 = fma(colk[i], cc[i], s0);
+        } else {
+          const T* up = S + (k - 1) * ld;  // a_{k-1}: u_{k-1} = s_{k-1} a_{k-1} below its unit entry
+          const T cf = coef[c], cs = cscl[c];
+          int i = k - 1 + g;
+          if (g == 0) {  // row k-1: the unit entry of u_{k-1}; gives R(k-1, c)
+            cc[k - 1] -= cf;
+            i += rg;
+          }
+          if (i == k) {  // row k: updated only (the unit entry of u_k enters in S1)
+            cc[k] = fma(-cs, up[k], cc[k]);
+            i += rg;
+          }
+          for (; i + rg < hl; i += 2 * rg) {
+            const T a0 = fma(-cs, up[i], cc[i]);
+            const T a1 = fma(-cs, up[i + rg], cc[i + rg]);
+            cc[i] = a0;
+            cc[i + rg] = a1;
+            s0 = fma(colk[i], a0, s0);
+            s1 = fma(colk[i + rg], a1, s1);
+          }
+          if (i < hl) {
+            const T a0 = fma(-cs, up[i], cc[i]);
+            cc[i] = a0;
+            s0 = fma(colk[i], a0, s0);
+          }
+        }
+        part[g * acols + slot] = s0 + s1;
+      }
     }
     __syncthreads();
-    const int acols = n - 1 - j;
     if (acols == 0) break;
-    const int rows = hl - j;  // rows j .. hl-1
-    int rg = NT / acols;
-    {
-      int byrows = rows / kLeafMinRows;
-      if (byrows < 1) byrows = 1;
-      if (rg > byrows) rg = byrows;
-      if (rg < 1) rg = 1;
-    }
-    const int chunk = (rows + rg - 1) / rg;
-    const int slot = tid % acols, g = tid / acols;
-    const int c = j + 1 + slot;
-    const int i0 = j + g * chunk;
-    const int i1 = min(i0 + chunk, hl);
-    // Phase A: partial dot products u_j^T a_c over this thread's rows.
-    if (g < rg) {
-      const T* cc = S + c * ld;
-      T s = T(0);
-      int i = i0;
-      if (i == j && i < i1) {
-        s = cc[j];
-        ++i;
-      }
-      for (; i < i1; ++i) s = fma(colj[i], cc[i], s);
-      part[g * acols + slot] = s;
-    }
-    __syncthreads();
-    // The rg partial sums of each column, once: coef_c = tau_j * w_c.
+    // S1: coefficients of H_k for the trailing columns.
     if (tid < acols) {
-      T w = T(0);
-      for (int gg = 0; gg < rg; ++gg) w += part[gg * acols + tid];
-      coefs[tid] = (T)tau_s[j] * w;
-    }
-    __syncthreads();
-    // Phase B: a_c -= coef_c u_j.
-    if (g < rg) {
-      const T coef = coefs[slot];
-      T* cc = S + c * ld;
-      int i = i0;
-      if (i == j && i < i1) {
-        cc[j] -= coef;
-        ++i;
+      int rg = NP / acols;
+      {
+        int byrows = (hl - k) / kLeafMinRows;
+        if (byrows < 1) byrows = 1;
+        if (rg > byrows) rg = byrows;
+        if (rg < 1) rg = 1;
       }
-      for (; i < i1; ++i) cc[i] -= coef * colj[i];
+      T d0 = T(0), d1 = T(0);
+      int gg = 0;
+      for (; gg + 1 < rg; gg += 2) {
+        d0 += part[gg * acols + tid];
+        d1 += part[(gg + 1) * acols + tid];
+      }
+      if (gg < rg) d0 += part[gg * acols + tid];
+      const int cidx = k + 1 + tid;
+      const double w = (double)S[cidx * ld + k] + sc_s[k] * (double)(d0 + d1);
+      const double cf = tau_s[k] * w;
+      coef[cidx] = (T)cf;
+      cscl[cidx] = (T)(cf * sc_s[k]);
     }
     __syncthreads();
+    // S2: column k+1 receives H_k; squared norm of its tail below row k+1.
+    if (warp < kS2Warps) {
+      T* ca = S + (k + 1) * ld;
+      const T cf = coef[k + 1], cs = cscl[k + 1];
+      double ss = 0.0;
+      if (tid == 0) ca[k] -= cf;
+      for (int i = k + 1 + tid; i < hl; i += 32 * kS2Warps) {
+        const T a = fma(-cs, colk[i], ca[i]);
+        ca[i] = a;
+        if (i > k + 1) ss = fma((double)a, (double)a, ss);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      if (lane == 0) wsum[warp] = ss;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  // Final values in the tile: Householder vectors u_k = s_k a_k below the
+  // diagonal, and R with the column factors taken back out (on and above).
+  for (int c = 0; c < n; ++c) {
+    T* col = S + c * ld;
+    const T fr = pow2_bits<T>(-cexp[c]);
+    const double sy = sc_s[c];
+    for (int i = tid; i < hl; i += NT) {
+      if (i <= c) col[i] = col[i] * fr;
+      else col[i] = sizeof(T) == 8 ? (T)((double)col[i] * sy) : col[i] * (T)sy;
+    }
   }
   __syncthreads();
 
@@ -150,13 +314,38 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
       const int P = t - Q * (Q + 1) / 2;
       const int p0 = 2 * P, q0 = 2 * Q;
       T z00 = T(0), z01 = T(0), z10 = T(0), z11 = T(0);
-      for (int i = q0; i < hl; ++i) {
+      // Rows q0 and q0 + 1 carry the unit diagonal (and zeros above it) of
+      // columns q0, q0 + 1 (and of p0, p0 + 1 when the tile is diagonal);
+      // below them every entry is a stored reflector element.
+      for (int i = q0; i < q0 + 2 && i < hl; ++i) {
         const T a0 = yv(i, p0), a1 = yv(i, p0 + 1);
         const T b0 = yv(i, q0), b1 = yv(i, q0 + 1);
         z00 = fma(a0, b0, z00);
         z01 = fma(a0, b1, z01);
         z10 = fma(a1, b0, z10);
         z11 = fma(a1, b1, z11);
+      }
+      if (q0 + 1 < n) {
+        const T* y0 = S + p0 * ld;
+        const T* y1 = S + (p0 + 1) * ld;
+        const T* x0 = S + q0 * ld;
+        const T* x1 = S + (q0 + 1) * ld;
+        for (int i = q0 + 2; i < hl; ++i) {
+          const T a0 = y0[i], a1 = y1[i], b0 = x0[i], b1 = x1[i];
+          z00 = fma(a0, b0, z00);
+          z01 = fma(a0, b1, z01);
+          z10 = fma(a1, b0, z10);
+          z11 = fma(a1, b1, z11);
+        }
+      } else {
+        for (int i = q0 + 2; i < hl; ++i) {
+          const T a0 = yv(i, p0), a1 = yv(i, p0 + 1);
+          const T b0 = yv(i, q0), b1 = yv(i, q0 + 1);
+          z00 = fma(a0, b0, z00);
+          z01 = fma(a0, b1, z01);
+          z10 = fma(a1, b0, z10);
+          z11 = fma(a1, b1, z11);
+        }
       }
       zacc[k][0] = z00;
       zacc[k][1] = z01;
