@@ -10,6 +10,7 @@
 namespace tsqr {
 
 constexpr int kLeafMinRows = 8;
+constexpr int kLeafMaxGroups = 8;  // row groups per column in the leaf update phase
 
 __host__ __device__ inline size_t leaf_align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -25,8 +26,8 @@ __host__ __device__ inline size_t leaf_tile_region(int n, int ld, size_t elem) {
 // region, NT partial dots, two per-column coefficient vectors, and FP64
 // per-column scalars (tau, reflector scale) plus 32 per-warp partial norms.
 __host__ __device__ inline size_t leaf_smem_bytes(int n, int ld, size_t elem, int nt) {
-  return leaf_tile_region(n, ld, elem) + leaf_align_up(elem * (size_t)nt, 8) + 2 * leaf_align_up(elem * (size_t)n, 8) +
-         sizeof(double) * (3 * (size_t)n + 32);
+  return leaf_tile_region(n, ld, elem) + leaf_align_up(elem * 3 * (size_t)nt, 8) + 2 * leaf_align_up(elem * (size_t)n, 8) +
+         sizeof(double) * (3 * (size_t)n + 128);
 }
 
 // Exponent k of the power of two 2^k that brings the largest magnitude of a
@@ -49,6 +50,15 @@ template <typename T>
 __device__ __forceinline__ T pow2_bits(int k) {
   if constexpr (sizeof(T) == 8) return __longlong_as_double((long long)(k + 1023) << 52);
   else return __int_as_float((k + 127) << 23);
+}
+
+// Row groups for a phase with `threads` threads per column (or pair) over
+// `rows` rows: at least one, and at least kLeafMinRows rows per group.
+__device__ __forceinline__ int leaf_groups(int threads, int rows) {
+  int byrows = rows / kLeafMinRows;
+  if (byrows < 1) byrows = 1;
+  int rg = threads < byrows ? threads : byrows;
+  return rg < 1 ? 1 : rg;
 }
 
 // Factors one leaf: rows Ag[0..hl) (column stride lda) of an n-column matrix,
@@ -78,20 +88,20 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   static_assert(NT >= 128, "the leaf schedule needs at least four warps");
   T* S = reinterpret_cast<T*>(smem);
   unsigned char* aux = smem + leaf_tile_region(n, ld, sizeof(T));
-  T* part = reinterpret_cast<T*>(aux);  // NT partial dots
-  T* coef = reinterpret_cast<T*>(aux + leaf_align_up(sizeof(T) * NT, 8));  // n: tau_k w_c
+  T* part = reinterpret_cast<T*>(aux);  // 3 NT partial dots (update warps, then the two of each Z pair)
+  T* coef = reinterpret_cast<T*>(aux + leaf_align_up(sizeof(T) * 3 * NT, 8));  // n: tau_k w_c
   T* cscl = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(coef) + leaf_align_up(sizeof(T) * n, 8));  // n: tau_k w_c s_k
   double* tau_s = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(cscl) + leaf_align_up(sizeof(T) * n, 8));
   double* sc_s = tau_s + n;  // n: reflector scales s_k
   int* cexp = reinterpret_cast<int*>(sc_s + n);  // n: column scaling exponents (n doubles reserved)
-  double* wsum = sc_s + 2 * n;  // 32 per-warp partial squared norms
+  double* wsum = sc_s + 2 * n;  // 128 per-lane partial squared norms (the S2 warps' lanes)
   T* Tm = reinterpret_cast<T*>(smem);  // n x n, after write-back
   T* Wt = Tm + (size_t)n * n;          // doubling workspace
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int kWarps = NT / 32;
   constexpr int kS2Warps = 4;           // warps of the single-column phase S2
-  constexpr int NP = NT - 32;           // threads of phase P (all but warp 0)
+  constexpr int kPWarps = kWarps - 1;   // warps of phase P (all but warp 0)
 
   // Load the tile: each thread walks the column-major elements e = tid + t NT,
   // several loads in flight.
@@ -151,29 +161,45 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
     for (int i = tid; i < hl; i += NT) col[i] *= f;
   }
   __syncthreads();
-  // Squared norm of column 0's tail, per S2 warp.
+  // Squared norm of column 0's tail, per S2 lane.
   if (warp < kS2Warps) {
     double ss = 0.0;
     for (int i = 1 + tid; i < hl; i += 32 * kS2Warps) {
       const double x = (double)S[i];
       ss = fma(x, x, ss);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) wsum[warp] = ss;
+    wsum[tid] = ss;
   }
   __syncthreads();
 
+  // Z = strictly-upper(Y^T Y), needed for T, is taken inside the loop:
+  //   Z(p, q) = u_p^T u_q = s_p (a_p(q) + s_q a_p(q+1:)^T a_q(q+1:)),  p < q,
+  // as soon as a_q's tail is final (step q), in pairs (p, p+1) per work item.
+  // Its work grows with q while the update work shrinks, so the two together
+  // keep phase P large at every step.  Z goes to Tg (global, read back for T).
+  //
+  // Work items of phase P: (column, row group) for the updates, then, from
+  // the next warp boundary on, (pair, row group) for Z.  Every column or pair
+  // gets the same number rg <= kLeafMaxGroups of row groups: one or two
+  // warps per SM sub-partition already keep its FP64 pipe busy, and fewer
+  // partial sums shorten the reductions of S1, which no other work overlaps.
   for (int k = 0; k < n; ++k) {
     T* colk = S + k * ld;
-    const int acols = n - 1 - k;  // trailing columns k+1 .. n-1
+    const int acols = n - 1 - k;     // trailing columns k+1 .. n-1
+    const int npairs = (k + 1) / 2;  // Z pairs of column k
+    int rg = acols + npairs > 0 ? (32 * kPWarps) / (acols + npairs) : 1;
+    rg = leaf_groups(rg < kLeafMaxGroups ? rg : kLeafMaxGroups, hl - k);
+    const int nu = acols * rg;                // update items
+    const int zbase = (nu + 31) / 32 * 32;    // first Z item
+    const int nitems = zbase + npairs * rg;
     if (warp == 0) {
-      // Reflector k (lane 0), from alpha = a_k(k) and the per-warp squared
-      // norms of a_k's tail.  Nothing else reads a_k(k) in this phase.
-      if (lane == 0) {
-        double ssq = 0.0;
+      // Reflector k, from alpha = a_k(k) and the per-lane squared norms of
+      // a_k's tail (summed by this warp, off the path of the other phases).
+      // Nothing else reads a_k(k) in this phase.
+      double ssq = (wsum[lane] + wsum[lane + 32]) + (wsum[lane + 64] + wsum[lane + 96]);
 #pragma unroll
-        for (int w = 0; w < kS2Warps; ++w) ssq += wsum[w];
+      for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+      if (lane == 0) {
         const double alpha = (double)colk[k];
         const int len = hl - k - 1;
         Reflector r = make_reflector(
@@ -184,83 +210,110 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
         colk[k] = (T)r.beta;
       }
       __syncwarp();
-    } else if (acols > 0) {
-      // P: H_{k-1} on column c and the partial dot with a_k's tail, rows
-      // interleaved over the rg groups (group g takes rows k-1+g, k-1+g+rg, ...).
-      const int ptid = tid - 32;
-      int rg = NP / acols;
-      {
-        int byrows = (hl - k) / kLeafMinRows;
-        if (byrows < 1) byrows = 1;
-        if (rg > byrows) rg = byrows;
-        if (rg < 1) rg = 1;
-      }
-      const int slot = ptid % acols, g = ptid / acols;
-      const int c = k + 1 + slot;
-      if (g < rg) {
-        T* cc = S + c * ld;
-        T s0 = T(0), s1 = T(0);
-        if (k == 0) {
-          int i = 1 + g;
+    } else {
+      for (int item = tid - 32; item < nitems; item += 32 * kPWarps) {
+        if (item < nu) {
+          // Update item: H_{k-1} on column c and the partial dot with a_k's
+          // tail, rows interleaved over the rg groups (group g takes rows
+          // k-1+g, k-1+g+rg, ...).
+          const int slot = item % acols, g = item / acols;
+          const int c = k + 1 + slot;
+          T* cc = S + c * ld;
+          T s0 = T(0), s1 = T(0);
+          if (k == 0) {
+            int i = 1 + g;
+            for (; i + rg < hl; i += 2 * rg) {
+              s0 = fma(colk[i], cc[i], s0);
+              s1 = fma(colk[i + rg], cc[i + rg], s1);
+            }
+            if (i < hl) s0 = fma(colk[i], cc[i], s0);
+          } else {
+            const T* up = S + (k - 1) * ld;  // a_{k-1}: u_{k-1} = s_{k-1} a_{k-1} below its unit entry
+            const T cf = coef[c], cs = cscl[c];
+            int i = k - 1 + g;
+            if (g == 0) {  // row k-1: the unit entry of u_{k-1}; gives R(k-1, c)
+              cc[k - 1] -= cf;
+              i += rg;
+            }
+            if (i == k) {  // row k: updated only (the unit entry of u_k enters in S1)
+              cc[k] = fma(-cs, up[k], cc[k]);
+              i += rg;
+            }
+            for (; i + rg < hl; i += 2 * rg) {
+              const T a0 = fma(-cs, up[i], cc[i]);
+              const T a1 = fma(-cs, up[i + rg], cc[i + rg]);
+              cc[i] = a0;
+              cc[i + rg] = a1;
+              s0 = fma(colk[i], a0, s0);
+              s1 = fma(colk[i + rg], a1, s1);
+            }
+            if (i < hl) {
+              const T a0 = fma(-cs, up[i], cc[i]);
+              cc[i] = a0;
+              s0 = fma(colk[i], a0, s0);
+            }
+          }
+          part[g * acols + slot] = s0 + s1;
+        } else if (item >= zbase) {
+          // Z item: partial dots of a_k's tail with a_p and a_p2.
+          const int zi = item - zbase;
+          const int t = zi % npairs, g = zi / npairs;
+          const int p = 2 * t, p2 = 2 * t + 1 < k ? 2 * t + 1 : 2 * t;
+          const T* x1 = S + p * ld;
+          const T* x2 = S + p2 * ld;
+          T z1 = T(0), z2 = T(0), z3 = T(0), z4 = T(0);
+          int i = k + 1 + g;
           for (; i + rg < hl; i += 2 * rg) {
-            s0 = fma(colk[i], cc[i], s0);
-            s1 = fma(colk[i + rg], cc[i + rg], s1);
-          }
-          if (i < hl) s0 = fma(colk[i], cc[i], s0);
-        } else {
-          const T* up = S + (k - 1) * ld;  // a_{k-1}: u_{k-1} = s_{k-1} a_{k-1} below its unit entry
-          const T cf = coef[c], cs = cscl[c];
-          int i = k - 1 + g;
-          if (g == 0) {  // row k-1: the unit entry of u_{k-1}; gives R(k-1, c)
-            cc[k - 1] -= cf;
-            i += rg;
-          }
-          if (i == k) {  // row k: updated only (the unit entry of u_k enters in S1)
-            cc[k] = fma(-cs, up[k], cc[k]);
-            i += rg;
-          }
-          for (; i + rg < hl; i += 2 * rg) {
-            const T a0 = fma(-cs, up[i], cc[i]);
-            const T a1 = fma(-cs, up[i + rg], cc[i + rg]);
-            cc[i] = a0;
-            cc[i + rg] = a1;
-            s0 = fma(colk[i], a0, s0);
-            s1 = fma(colk[i + rg], a1, s1);
+            const T v0 = colk[i], v1 = colk[i + rg];
+            z1 = fma(v0, x1[i], z1);
+            z2 = fma(v0, x2[i], z2);
+            z3 = fma(v1, x1[i + rg], z3);
+            z4 = fma(v1, x2[i + rg], z4);
           }
           if (i < hl) {
-            const T a0 = fma(-cs, up[i], cc[i]);
-            cc[i] = a0;
-            s0 = fma(colk[i], a0, s0);
+            z1 = fma(colk[i], x1[i], z1);
+            z2 = fma(colk[i], x2[i], z2);
           }
+          part[NT + g * npairs + t] = z1 + z3;
+          part[2 * NT + g * npairs + t] = z2 + z4;
         }
-        part[g * acols + slot] = s0 + s1;
+      }
+    }
+    __syncthreads();
+    // S1: coefficients of H_k for the trailing columns (threads 0..acols-1),
+    // and the Z entries of column k (threads from the next warp boundary on,
+    // so that no warp does both).
+    {
+      const int zs1 = (acols + 31) / 32 * 32;
+      for (int sl = tid; sl < zs1 + npairs; sl += NT) {
+        if (sl < acols) {
+          T d0 = T(0), d1 = T(0);
+          int gg = 0;
+          for (; gg + 1 < rg; gg += 2) {
+            d0 += part[gg * acols + sl];
+            d1 += part[(gg + 1) * acols + sl];
+          }
+          if (gg < rg) d0 += part[gg * acols + sl];
+          const int cidx = k + 1 + sl;
+          const double tk = tau_s[k], sk = sc_s[k], ts = tk * sk;
+          const double w = fma(sk, (double)(d0 + d1), (double)S[cidx * ld + k]);
+          coef[cidx] = (T)(tk * w);
+          cscl[cidx] = (T)(ts * w);
+        } else if (sl >= zs1) {
+          const int t = sl - zs1;
+          T d1 = T(0), d2 = T(0);
+          for (int gg = 0; gg < rg; ++gg) {
+            d1 += part[NT + gg * npairs + t];
+            d2 += part[2 * NT + gg * npairs + t];
+          }
+          const int p = 2 * t, p2 = 2 * t + 1;
+          Tg[p + k * n] = (T)(sc_s[p] * ((double)S[p * ld + k] + sc_s[k] * (double)d1));
+          if (p2 < k) Tg[p2 + k * n] = (T)(sc_s[p2] * ((double)S[p2 * ld + k] + sc_s[k] * (double)d2));
+        }
       }
     }
     __syncthreads();
     if (acols == 0) break;
-    // S1: coefficients of H_k for the trailing columns.
-    if (tid < acols) {
-      int rg = NP / acols;
-      {
-        int byrows = (hl - k) / kLeafMinRows;
-        if (byrows < 1) byrows = 1;
-        if (rg > byrows) rg = byrows;
-        if (rg < 1) rg = 1;
-      }
-      T d0 = T(0), d1 = T(0);
-      int gg = 0;
-      for (; gg + 1 < rg; gg += 2) {
-        d0 += part[gg * acols + tid];
-        d1 += part[(gg + 1) * acols + tid];
-      }
-      if (gg < rg) d0 += part[gg * acols + tid];
-      const int cidx = k + 1 + tid;
-      const double w = (double)S[cidx * ld + k] + sc_s[k] * (double)(d0 + d1);
-      const double cf = tau_s[k] * w;
-      coef[cidx] = (T)cf;
-      cscl[cidx] = (T)(cf * sc_s[k]);
-    }
-    __syncthreads();
     // S2: column k+1 receives H_k; squared norm of its tail below row k+1.
     if (warp < kS2Warps) {
       T* ca = S + (k + 1) * ld;
@@ -272,13 +325,10 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
         ca[i] = a;
         if (i > k + 1) ss = fma((double)a, (double)a, ss);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) wsum[warp] = ss;
+      wsum[tid] = ss;
     }
     __syncthreads();
   }
-  __syncthreads();
   // Final values in the tile: Householder vectors u_k = s_k a_k below the
   // diagonal, and R with the column factors taken back out (on and above).
   for (int c = 0; c < n; ++c) {
@@ -291,68 +341,6 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
     }
   }
   __syncthreads();
-
-  // Z = strictly-upper(Y^T Y) in registers: 2x2 tiles (P, Q) with P <= Q
-  // over the upper triangle of n/2 x n/2 tile blocks, tile t = tid + k*NT.
-  const int nb = (n + 1) / 2;
-  const int ntiles = nb * (nb + 1) / 2;
-  constexpr int kMaxTiles = (NMAX / 2) * (NMAX / 2 + 1) / 2 / NT + 1;
-  T zacc[kMaxTiles][4];
-  auto yv = [&](int i, int col) -> T {
-    if (col >= n || i < col) return T(0);
-    return i == col ? T(1) : S[col * ld + i];
-  };
-#pragma unroll
-  for (int k = 0; k < kMaxTiles; ++k) {
-    zacc[k][0] = zacc[k][1] = zacc[k][2] = zacc[k][3] = T(0);
-    const int t = tid + k * NT;
-    if (t < ntiles) {
-      // t -> (P, Q) with P <= Q, ordered by Q so that the lanes of a warp
-      // loop over nearly the same rows [2Q, hl).
-      int Q = 0;
-      while ((Q + 1) * (Q + 2) / 2 <= t) ++Q;
-      const int P = t - Q * (Q + 1) / 2;
-      const int p0 = 2 * P, q0 = 2 * Q;
-      T z00 = T(0), z01 = T(0), z10 = T(0), z11 = T(0);
-      // Rows q0 and q0 + 1 carry the unit diagonal (and zeros above it) of
-      // columns q0, q0 + 1 (and of p0, p0 + 1 when the tile is diagonal);
-      // below them every entry is a stored reflector element.
-      for (int i = q0; i < q0 + 2 && i < hl; ++i) {
-        const T a0 = yv(i, p0), a1 = yv(i, p0 + 1);
-        const T b0 = yv(i, q0), b1 = yv(i, q0 + 1);
-        z00 = fma(a0, b0, z00);
-        z01 = fma(a0, b1, z01);
-        z10 = fma(a1, b0, z10);
-        z11 = fma(a1, b1, z11);
-      }
-      if (q0 + 1 < n) {
-        const T* y0 = S + p0 * ld;
-        const T* y1 = S + (p0 + 1) * ld;
-        const T* x0 = S + q0 * ld;
-        const T* x1 = S + (q0 + 1) * ld;
-        for (int i = q0 + 2; i < hl; ++i) {
-          const T a0 = y0[i], a1 = y1[i], b0 = x0[i], b1 = x1[i];
-          z00 = fma(a0, b0, z00);
-          z01 = fma(a0, b1, z01);
-          z10 = fma(a1, b0, z10);
-          z11 = fma(a1, b1, z11);
-        }
-      } else {
-        for (int i = q0 + 2; i < hl; ++i) {
-          const T a0 = yv(i, p0), a1 = yv(i, p0 + 1);
-          const T b0 = yv(i, q0), b1 = yv(i, q0 + 1);
-          z00 = fma(a0, b0, z00);
-          z01 = fma(a0, b1, z01);
-          z10 = fma(a1, b0, z10);
-          z11 = fma(a1, b1, z11);
-        }
-      }
-      zacc[k][0] = z00;
-      zacc[k][1] = z01;
-      zacc[k][2] = z10;
-      zacc[k][3] = z11;
-    }
-  }
   // Write back Y (below the diagonal) and R_i (on and above) in place, the
   // leaf R factor to the tree's level-0 items, and tau.
   for (int cc = 0; cc < n; ++cc) {
@@ -365,26 +353,10 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   }
   for (int cc = tid; cc < n; cc += NT) taul[cc] = (T)tau_s[cc];
   __syncthreads();
-  // Tm = Z above the diagonal, tau on it, zero below.
+  // Tm = Z above the diagonal (from Tg), tau on it, zero below.
   for (int idx = tid; idx < n * n; idx += NT) {
     const int p = idx % n, q = idx / n;
-    Tm[idx] = p == q ? (T)tau_s[p] : T(0);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < kMaxTiles; ++k) {
-    const int t = tid + k * NT;
-    if (t < ntiles) {
-      int Q = 0;
-      while ((Q + 1) * (Q + 2) / 2 <= t) ++Q;
-      const int P = t - Q * (Q + 1) / 2;
-      const int p0 = 2 * P, q0 = 2 * Q;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int p = p0 + (e >> 1), q = q0 + (e & 1);
-        if (p < q && q < n) Tm[p + q * n] = zacc[k][e];
-      }
-    }
+    Tm[idx] = p == q ? (T)tau_s[p] : (p < q ? Tg[idx] : T(0));
   }
   __syncthreads();
   build_t_doubling(Tm, Wt, n);
