@@ -146,13 +146,14 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
   int64_t h = opts && opts->leaf_rows > 0 ? opts->leaf_rows : 0;
   if (h == 0) {
     // Tallest leaf (a multiple of 32 rows, at most 1024) whose n-column tile
-    // fits in about 200 KB of shared memory: taller leaves mean fewer tree
-    // nodes (the tree's work is about n / (2h) of the leaves') and a smaller
-    // n^3 share in forming Q, at one leaf CTA per SM.
+    // and working buffers fit in one SM's shared memory (the loop below
+    // shrinks it until they do): taller leaves mean fewer tree nodes (the
+    // tree's work is about n / (2h) of the leaves') and a smaller n^3 share
+    // in forming Q, at one leaf CTA per SM.
     // FP32 leaves are cheap in arithmetic and latency-bound, so they keep
     // 68 KB tiles (three 256-thread CTAs per SM) instead.
     if (q->es == 8) {
-      h = 200 * 1024 / 8 / n / 32 * 32;
+      h = smax / 8 / n / 32 * 32;
       if (h > 1024) h = 1024;
     } else {
       h = 1;

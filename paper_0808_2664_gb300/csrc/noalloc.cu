@@ -77,7 +77,7 @@ extern "C" int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t ld
   if (m == 0 || n == 0) return TSQR_OK;
   if (n > kMaxN) return TSQR_ERR_UNSUPPORTED;
 
-  // The library's default plan: leaf height h, binary tree.
+  // A fixed plan: leaves of a power-of-two height within 68 KB, binary tree.
   int64_t h = 1;
   while (h * 2 <= (68 * 1024 / 8) / n && h * 2 <= 1024) h *= 2;
   if (h < n) h = n;
