@@ -1,0 +1,390 @@
+// Binary tree-node QR of stacked triangles, G nodes per CTA in lock step.
+//
+// A node factors [R_0; R_1] (two upper-triangular n x n children) with
+// structured Householder QR (Section 2.1, Eqs. TSQR_binarytree_2/_3, and the
+// remark on structured local QR): reflector k touches row k of R_0 and rows
+// 0..k of R_1, so its vector is e_k on top and an upper-triangular column
+// y_k below; nothing below the triangles is stored or touched (2n^3/3 flops
+// per node, Section 2.2).  The node's Y is the upper triangle that replaced
+// R_1.
+//
+// A node has little work per column (at most n^2/2 products) behind a
+// serial chain per column (reflector, coefficients), so this kernel
+//   * factors G nodes of a tree level together, so that each serial step
+//     serves G nodes at once (lane g of warp 0 forms node g's reflector);
+//   * uses the leaf kernel's schedule: the reflector of column k is formed
+//     by warp 0 while the other warps apply H_{k-1} to every trailing column
+//     fused with that column's dot with column k's unscaled tail, and take
+//     the entries Z(p, k) = u_p^T u_k of the T factor as extra work items;
+//     then one warp per node turns the partial dots into coefficients and
+//     carries column k+1 through H_k and its squared norm; two barriers per
+//     column;
+//   * stores the triangles packed (column c of a block holds rows 0..c), so
+//     that a node takes n(n+1) values of shared memory.
+// Each column is first scaled by a power of two bringing its largest entry
+// (over both triangles) to [1/2, 1); Householder QR commutes exactly with
+// that, and it keeps the unscaled dot products in range.  Products are in
+// the storage type T; squared norms and reflector scalars in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "leaf_device.cuh"
+#include "reflector.cuh"
+#include "tsqr_internal.cuh"
+
+namespace tsqr {
+
+constexpr int kNode2MaxGroups = 4;  // row groups per column in the update phase
+constexpr int kNode2MinRows = 4;    // rows per group at least
+
+__host__ __device__ inline int node2_packed(int n) { return n * (n + 1) / 2; }
+
+// Bytes of one node's compact-WY doubling workspace (T, then n^2/2 + 1).
+__host__ __device__ inline size_t node2_t_bytes(int n, size_t elem) {
+  return leaf_align_up(elem * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
+}
+
+// The region holding G nodes' packed triangles, reused for the T builds.
+__host__ __device__ inline size_t node2_region_bytes(int n, int G, size_t elem) {
+  const size_t data = leaf_align_up(elem * 2 * (size_t)G * node2_packed(n), 16);
+  const size_t tb = node2_t_bytes(n, elem);
+  return data > tb ? data : tb;
+}
+
+__host__ __device__ inline size_t node2_smem_bytes(int n, int G, size_t elem, int nt) {
+  return node2_region_bytes(n, G, elem) + leaf_align_up(elem * 3 * (size_t)nt, 8) +
+         2 * leaf_align_up(elem * (size_t)G * n, 8) + sizeof(double) * (3 * (size_t)G * n + 32);
+}
+
+// T for `count` nodes at once: Tm_g = base + g * stride holds tau on the
+// diagonal, Z above it and zeros below; Wt_g = Tm_g + n^2 is the workspace.
+// The same merges as build_t_doubling, with the work items of all nodes
+// spread over the block.
+template <typename T>
+__device__ __forceinline__ void build_t_doubling_batch(T* base, size_t stride, int count, int n) {
+  for (int b = 1; b < n; b *= 2) {
+    const int npairs = (n + 2 * b - 1) / (2 * b);
+    const int bb = b * b;
+    const int per = npairs * bb;
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+      const int g = idx / per, r0 = idx - g * per;
+      const int pair = r0 / bb, rem = r0 % bb;
+      const int pl = rem % b, ql = rem / b;
+      const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
+      if (q >= n) continue;
+      const T* Tm = base + g * stride;
+      T* Wt = base + g * stride + (size_t)n * n;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int r = s + b;
+      for (; r + 3 <= q; r += 4) {
+        a0 = fma(Tm[p + r * n], Tm[r + q * n], a0);
+        a1 = fma(Tm[p + (r + 1) * n], Tm[r + 1 + q * n], a1);
+        a2 = fma(Tm[p + (r + 2) * n], Tm[r + 2 + q * n], a2);
+        a3 = fma(Tm[p + (r + 3) * n], Tm[r + 3 + q * n], a3);
+      }
+      for (; r <= q; ++r) a0 = fma(Tm[p + r * n], Tm[r + q * n], a0);
+      Wt[pair * bb + pl + ql * b] = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+      const int g = idx / per, r0 = idx - g * per;
+      const int pair = r0 / bb, rem = r0 % bb;
+      const int ql = rem % b, pl = rem / b;
+      const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
+      if (q >= n) continue;
+      T* Tm = base + g * stride;
+      const T* Wt = base + g * stride + (size_t)n * n;
+      const T* w = Wt + pair * bb + ql * b - s;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int r = p;
+      for (; r + 3 < s + b; r += 4) {
+        a0 = fma(Tm[p + r * n], w[r], a0);
+        a1 = fma(Tm[p + (r + 1) * n], w[r + 1], a1);
+        a2 = fma(Tm[p + (r + 2) * n], w[r + 2], a2);
+        a3 = fma(Tm[p + (r + 3) * n], w[r + 3], a3);
+      }
+      for (; r < s + b; ++r) a0 = fma(Tm[p + r * n], w[r], a0);
+      Tm[p + q * n] = -((a0 + a1) + (a2 + a3));
+    }
+    __syncthreads();
+  }
+}
+
+// Factors nodes node0 .. node0+G-1 of a binary tree level: children
+// Rin[2 node], Rin[2 node + 1] (n x n, ld n, upper part read with
+// L1-bypassing loads; a missing second child reads as zeros, which gives
+// tau = 0, Y = 0 and R = the lone child), outputs as node_factor_one with
+// kBuildT: R (Ro), Y (one n x n block), tau and T.  Nodes at or past `nodes`
+// are computed on zeros and not written.  Every thread of the block calls it.
+template <typename T, int NT, int G>
+__device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64_t nodes, int64_t node0, int n,
+                                   T* Rout, T* Yout, T* Tout, T* tauout, int* status, unsigned char* smem) {
+  static_assert(NT / 32 >= G + 2, "need a reflector warp, one column warp per node and a Z warp");
+  const int pk = node2_packed(n);
+  T* D = reinterpret_cast<T*>(smem);
+  unsigned char* aux = smem + node2_region_bytes(n, G, sizeof(T));
+  T* part = reinterpret_cast<T*>(aux);  // 3 NT partial dots
+  T* coef = reinterpret_cast<T*>(aux + leaf_align_up(sizeof(T) * 3 * NT, 8));  // G n: tau_k w_c
+  T* cscl = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(coef) + leaf_align_up(sizeof(T) * G * n, 8));
+  double* tau_s = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(cscl) + leaf_align_up(sizeof(T) * G * n, 8));
+  double* sc_s = tau_s + G * n;                         // G n: reflector scales
+  int* cexp = reinterpret_cast<int*>(sc_s + G * n);     // G n: column exponents (G n doubles reserved)
+  double* ssq = sc_s + 2 * G * n;                       // G: squared tail norms
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int kPWarps = NT / 32 - 1;
+  const int64_t nn = (int64_t)n * n;
+  // Column c of block b (0: R_0, 1: R_1) of node g, rows 0..c.
+  auto col = [&](int g, int b, int c) -> T* { return D + (size_t)(2 * g + b) * pk + c * (c + 1) / 2; };
+
+  // Load the children's upper triangles, one warp per (node, column): both
+  // triangles' column c (rows 0..c), its largest magnitude, its power-of-two
+  // factor applied on the way into shared memory.
+  for (int gc = warp; gc < G * n; gc += NT / 32) {
+    const int g = gc / n, c = gc - g * n;
+    const int64_t node = node0 + g;
+    const bool has0 = node < nodes, has1 = node < nodes && 2 * node + 1 < nin;
+    const T* src0 = Rin + (2 * node) * nn + (int64_t)c * n;
+    const T* src1 = src0 + nn;
+    T v0[kMaxN / 32], v1[kMaxN / 32];
+    unsigned mx = 0u;
+#pragma unroll
+    for (int r = 0; r < kMaxN / 32; ++r) {
+      const int i = lane + 32 * r;
+      v0[r] = T(0);
+      v1[r] = T(0);
+      if (i <= c) {
+        if (has0) v0[r] = __ldcg(src0 + i);
+        if (has1) v1[r] = __ldcg(src1 + i);
+        const unsigned b0 = sizeof(T) == 8 ? (unsigned)__double2hiint((double)v0[r]) : __float_as_uint((float)v0[r]);
+        const unsigned b1 = sizeof(T) == 8 ? (unsigned)__double2hiint((double)v1[r]) : __float_as_uint((float)v1[r]);
+        const unsigned m0 = b0 & 0x7fffffffu, m1 = b1 & 0x7fffffffu;
+        mx = m0 > mx ? m0 : mx;
+        mx = m1 > mx ? m1 : mx;
+      }
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    const int ex = column_exp2<T>(mx);
+    const T f = pow2_bits<T>(ex);
+    if (lane == 0) cexp[gc] = ex;
+    T* d0 = col(g, 0, c);
+    T* d1 = col(g, 1, c);
+#pragma unroll
+    for (int r = 0; r < kMaxN / 32; ++r) {
+      const int i = lane + 32 * r;
+      if (i <= c) {
+        d0[i] = v0[r] * f;
+        d1[i] = v1[r] * f;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid < G) {
+    const double x = (double)col(tid, 1, 0)[0];
+    ssq[tid] = x * x;
+  }
+  __syncthreads();
+
+  for (int k = 0; k < n; ++k) {
+    const int acols = n - 1 - k;     // trailing columns k+1 .. n-1
+    const int npairs = (k + 1) / 2;  // Z pairs (p, p+1), p < k, of column k
+    int rg = (32 * kPWarps) / (G * (acols + npairs) > 0 ? G * (acols + npairs) : 1);
+    {
+      int byrows = (k + 1) / kNode2MinRows;
+      if (byrows < 1) byrows = 1;
+      if (rg > byrows) rg = byrows;
+      if (rg > kNode2MaxGroups) rg = kNode2MaxGroups;
+      if (rg < 1) rg = 1;
+    }
+    const int ucols = G * acols, zcols = G * npairs;
+    const int nu = ucols * rg;
+    const int zbase = (nu + 31) / 32 * 32;
+    const int nitems = zbase + zcols * rg;
+    if (warp == 0) {
+      // Reflector k of node g (lane g): alpha = R_0(k, k), tail = R_1(0..k, k).
+      if (lane < G) {
+        const int g = lane;
+        T* ck0 = col(g, 0, k);
+        const T* ck1 = col(g, 1, k);
+        const double alpha = (double)ck0[k];
+        Reflector r = make_reflector_fast(
+            alpha, ssq[g], [&]() { return scaled_norm(k + 1, [&](int i) { return (double)ck1[i]; }); }, status);
+        tau_s[g * n + k] = r.tau;
+        sc_s[g * n + k] = r.scale;
+        ck0[k] = (T)r.beta;
+      }
+      __syncwarp();
+    } else {
+      for (int item = tid - 32; item < nitems; item += 32 * kPWarps) {
+        if (item < nu) {
+          // H_{k-1} on trailing column c (R_0 row k-1; R_1 rows 0..k-1) fused
+          // with the partial dot of R_1 rows 0..k with column k's tail.
+          const int slot = item % ucols, grp = item / ucols;
+          const int g = slot / acols, c = k + 1 + slot % acols;
+          T* cc1 = col(g, 1, c);
+          const T* ak = col(g, 1, k);
+          T s0 = T(0), s1 = T(0);
+          if (k == 0) {
+            if (grp == 0) s0 = ak[0] * cc1[0];
+          } else {
+            const T* up = col(g, 1, k - 1);
+            const T cf = coef[g * n + c], cs = cscl[g * n + c];
+            if (grp == 0) col(g, 0, c)[k - 1] -= cf;  // the unit entry of u_{k-1}: R(k-1, c)
+            int i = grp;
+            for (; i + rg < k; i += 2 * rg) {
+              const T a0 = fma(-cs, up[i], cc1[i]);
+              const T a1 = fma(-cs, up[i + rg], cc1[i + rg]);
+              cc1[i] = a0;
+              cc1[i + rg] = a1;
+              s0 = fma(ak[i], a0, s0);
+              s1 = fma(ak[i + rg], a1, s1);
+            }
+            if (i < k) {
+              const T a0 = fma(-cs, up[i], cc1[i]);
+              cc1[i] = a0;
+              s0 = fma(ak[i], a0, s0);
+              i += rg;
+            }
+            if (i == k) s1 = fma(ak[k], cc1[k], s1);  // row k: not touched by H_{k-1}
+          }
+          part[grp * ucols + slot] = s0 + s1;
+        } else if (item >= zbase) {
+          // Z(p, k) and Z(p2, k): partial dots of R_1 columns over rows 0..p(2).
+          const int zi = item - zbase;
+          const int slot = zi % zcols, grp = zi / zcols;
+          const int g = slot / npairs, t = slot % npairs;
+          const int p = 2 * t, p2 = 2 * t + 1 < k ? 2 * t + 1 : 2 * t;
+          const T* ak = col(g, 1, k);
+          const T* x1 = col(g, 1, p);
+          const T* x2 = col(g, 1, p2);
+          T z1 = T(0), z2 = T(0);
+          for (int i = grp; i <= p2; i += rg) {
+            const T v = ak[i];
+            if (i <= p) z1 = fma(v, x1[i], z1);
+            z2 = fma(v, x2[i], z2);
+          }
+          part[NT + grp * zcols + slot] = z1;
+          part[2 * NT + grp * zcols + slot] = z2;
+        }
+      }
+    }
+    __syncthreads();
+    // S: warp 1 + g forms the coefficients of H_k for node g's trailing
+    // columns (lanes over columns), then applies H_k to column k+1 (its
+    // coefficient comes from lane 0 by shuffle) and sums the squared tail of
+    // that column for the next reflector: R_1 rows 0..k+1.  The remaining
+    // warps take the Z entries of column k.
+    if (warp >= 1 && warp <= G) {
+      const int g = warp - 1;
+      const double tk = tau_s[g * n + k], sk = sc_s[g * n + k], ts = tk * sk;
+      T cf1 = T(0), cs1 = T(0);
+      for (int j = lane; j < acols; j += 32) {
+        const int sl = g * acols + j;
+        T d0 = T(0), d1 = T(0);
+        int gg = 0;
+        for (; gg + 1 < rg; gg += 2) {
+          d0 += part[gg * ucols + sl];
+          d1 += part[(gg + 1) * ucols + sl];
+        }
+        if (gg < rg) d0 += part[gg * ucols + sl];
+        const int c = k + 1 + j;
+        const double w = fma(sk, (double)(d0 + d1), (double)col(g, 0, c)[k]);
+        const T cf = (T)(tk * w), cs = (T)(ts * w);
+        coef[g * n + c] = cf;
+        cscl[g * n + c] = cs;
+        if (j == 0) {
+          cf1 = cf;
+          cs1 = cs;
+        }
+      }
+      if (acols > 0) {
+        cf1 = __shfl_sync(0xffffffffu, cf1, 0);
+        cs1 = __shfl_sync(0xffffffffu, cs1, 0);
+        T* cc1 = col(g, 1, k + 1);
+        const T* ak = col(g, 1, k);
+        if (lane == 0) col(g, 0, k + 1)[k] -= cf1;
+        double ss = 0.0;
+        for (int i = lane; i <= k + 1; i += 32) {
+          T v = cc1[i];
+          if (i <= k) {
+            v = fma(-cs1, ak[i], v);
+            cc1[i] = v;
+          }
+          ss = fma((double)v, (double)v, ss);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) ssq[g] = ss;
+      }
+    } else if (warp > G) {
+      for (int zs = tid - 32 * (G + 1); zs < zcols; zs += NT - 32 * (G + 1)) {
+        const int g = zs / npairs, t = zs % npairs;
+        T d1 = T(0), d2 = T(0);
+        for (int gg = 0; gg < rg; ++gg) {
+          d1 += part[NT + gg * zcols + zs];
+          d2 += part[2 * NT + gg * zcols + zs];
+        }
+        const int64_t node = node0 + g;
+        if (node < nodes) {
+          T* Tg = Tout + node * nn;
+          const int p = 2 * t, p2 = 2 * t + 1;
+          const double sk = sc_s[g * n + k];
+          Tg[p + k * n] = (T)(sc_s[g * n + p] * sk * (double)d1);
+          if (p2 < k) Tg[p2 + k * n] = (T)(sc_s[g * n + p2] * sk * (double)d2);
+        }
+      }
+    }
+    __syncthreads();
+    if (acols == 0) break;
+  }
+  // Outputs, one warp per (node, column): R (column factors taken back
+  // out), Y = s_c * (R_1 column c), zeros below the diagonal; tau.
+  for (int gc = warp; gc < G * n; gc += NT / 32) {
+    const int g = gc / n, c = gc - g * n;
+    const int64_t node = node0 + g;
+    if (node < nodes) {
+      const T fr = pow2_bits<T>(-cexp[gc]);
+      const double sy = sc_s[gc];
+      const T* r0 = col(g, 0, c);
+      const T* r1 = col(g, 1, c);
+      T* ro = Rout + node * nn + (int64_t)c * n;
+      T* yo = Yout + node * nn + (int64_t)c * n;
+      for (int i = lane; i < n; i += 32) {
+        ro[i] = i <= c ? r0[i] * fr : T(0);
+        yo[i] = i <= c ? (T)((double)r1[i] * sy) : T(0);
+      }
+      if (lane == 0) tauout[node * n + c] = (T)tau_s[gc];
+    }
+  }
+  __syncthreads();
+  // T of each node: Z (from Tout) above the diagonal, tau on it; as many
+  // nodes at a time as the region holds.
+  const size_t tstride = node2_t_bytes(n, sizeof(T)) / sizeof(T);
+  const int per_batch = (int)(node2_region_bytes(n, G, sizeof(T)) / node2_t_bytes(n, sizeof(T)));
+  for (int g0 = 0; g0 < G; g0 += per_batch) {
+    const int cnt = G - g0 < per_batch ? G - g0 : per_batch;
+    for (int gq = warp; gq < cnt * n; gq += NT / 32) {
+      const int gl = gq / n, q = gq - gl * n, g = g0 + gl;
+      const int64_t node = node0 + g;
+      T* Tm = D + gl * tstride + (size_t)q * n;
+      for (int p = lane; p < n; p += 32) {
+        T v = T(0);
+        if (p == q) v = (T)tau_s[g * n + p];
+        else if (p < q && node < nodes) v = Tout[node * nn + (int64_t)q * n + p];
+        Tm[p] = v;
+      }
+    }
+    __syncthreads();
+    build_t_doubling_batch(D, tstride, cnt, n);
+    for (int gq = warp; gq < cnt * n; gq += NT / 32) {
+      const int gl = gq / n, q = gq - gl * n;
+      const int64_t node = node0 + g0 + gl;
+      if (node < nodes)
+        for (int p = lane; p < n; p += 32) Tout[node * nn + (int64_t)q * n + p] = D[gl * tstride + (size_t)q * n + p];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tsqr

@@ -14,6 +14,7 @@
 // 0 followed by rows 0..j of blocks 1..q-1.
 #include <cuda_runtime.h>
 
+#include "node2_device.cuh"
 #include "node_device.cuh"
 #include "tsqr_internal.cuh"
 
@@ -34,10 +35,50 @@ __global__ void __launch_bounds__(NT) node_factor_kernel(NodeFactorArgs<T> a) {
   }
 }
 
+// Binary levels: G nodes per CTA (node2_device.cuh), grid-stride over groups.
+template <typename T, int NT, int G>
+__global__ void __launch_bounds__(NT) node2_factor_kernel(NodeFactorArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int64_t groups = (a.nodes + G - 1) / G;
+  for (int64_t gi = blockIdx.x; gi < groups; gi += gridDim.x)
+    node2_factor_group<T, NT, G>(a.Rin, a.nin, a.nodes, gi * G, a.n, a.Rout, a.Y, a.Tw, a.tau, a.status, smem);
+}
+
+template <typename T, int NT, int G>
+cudaError_t launch_node2(const NodeFactorArgs<T>& a, int sms, cudaStream_t s) {
+  const size_t smem = node2_smem_bytes(a.n, G, sizeof(T), NT);
+  auto kern = node2_factor_kernel<T, NT, G>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t groups = (a.nodes + G - 1) / G;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > groups) grid = groups;
+  kern<<<(unsigned)grid, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t node2_factor_smem_max(int n, size_t elem) {
+  const size_t a = node2_smem_bytes(n, 1, elem, 256), b = node2_smem_bytes(n, 2, elem, 256);
+  return a > b ? a : b;
+}
+
 template <typename T>
 cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
   if (a.nodes <= 0 || a.n <= 0) return cudaSuccess;
+  if (a.arity == 2) {
+    // Wide levels: two nodes per CTA share each serial step; narrow levels
+    // (fewer groups than about two per SM): one node per CTA, least latency.
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (a.nodes >= 4 * (int64_t)sms) return launch_node2<T, 256, 2>(a, sms, s);
+    return launch_node2<T, 256, 1>(a, sms, s);
+  }
   const size_t smem = node_smem_bytes(a.n, a.arity, sizeof(T), kNodeThreads);
   auto kern = node_factor_kernel<T, kNodeThreads>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -53,7 +94,10 @@ cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-size_t node_factor_smem(int n, int q, size_t elem) { return node_smem_bytes(n, q, elem, kNodeThreads); }
+size_t node_factor_smem(int n, int q, size_t elem) {
+  if (q == 2) return node2_factor_smem_max(n, elem);
+  return node_smem_bytes(n, q, elem, kNodeThreads);
+}
 
 template cudaError_t launch_node_factor<double>(const NodeFactorArgs<double>&, cudaStream_t);
 template cudaError_t launch_node_factor<float>(const NodeFactorArgs<float>&, cudaStream_t);

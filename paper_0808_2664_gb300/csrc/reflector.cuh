@@ -66,6 +66,41 @@ __device__ __forceinline__ Reflector make_reflector(double alpha, double ssq, Re
   return r;
 }
 
+// The same reflector with a shorter chain of dependent FP64 operations, for
+// the serial step of each column.  FP64 arithmetic has a long dependent
+// latency on this GPU, and IEEE sqrt and division are long sequences of it;
+// here 1/||x|| and 1/|alpha - beta| start from FP32 estimates (rsqrtf and a
+// fast FP32 reciprocal, about 22 correct bits) and take one third-order
+// correction step each, the series (1 - e)^(-1/2) ~ 1 + e/2 + 3e^2/8 with
+// e = 1 - x y^2, and (1 - e)^(-1) ~ 1 + e + e^2 with e = 1 - d y (the
+// relative error goes from e to O(e^3)), which brings them to a few FP64
+// ulps.  Then
+//   ||x|| = x2 * (1/||x||),  tau = 1 + |alpha| / ||x||,
+//   scale = sign(alpha) / (|alpha| + ||x||),  beta = -sign(alpha) ||x||,
+// the formulas of make_reflector rewritten with those two reciprocals.
+// Used only where every quantity stays far inside FP32's range (the tail's
+// squared norm in [2^-100, 2^100], |alpha| <= 2^50); otherwise, and for
+// zero, non-finite or extreme inputs, make_reflector runs.
+template <class Rescan>
+__device__ __forceinline__ Reflector make_reflector_fast(double alpha, double ssq, Rescan rescan, int* status) {
+  const double aa = fabs(alpha);
+  if (!(ssq >= 0x1p-100 && ssq <= 0x1p100 && aa <= 0x1p50)) return make_reflector(alpha, ssq, rescan, status);
+  const double x2 = fma(alpha, alpha, ssq);
+  const double r0 = (double)rsqrtf((float)x2);
+  const double e = fma(-(x2 * r0), r0, 1.0);
+  const double r = fma(r0 * e, fma(0.375, e, 0.5), r0);  // 1 / ||x||
+  const double nrm = x2 * r;
+  const double ad = aa + nrm;  // |alpha - beta|
+  const double q0 = (double)__fdividef(1.0f, (float)ad);
+  const double f = fma(-ad, q0, 1.0);
+  const double q = fma(q0 * f, 1.0 + f, q0);  // 1 / |alpha - beta|
+  Reflector out;
+  out.beta = alpha >= 0.0 ? -nrm : nrm;
+  out.scale = alpha >= 0.0 ? q : -q;
+  out.tau = fma(aa, r, 1.0);
+  return out;
+}
+
 // Scaled 2-norm over a strided sequence produced by `get(i)`, i in [0, len).
 template <class Get>
 __device__ __forceinline__ double scaled_norm(int len, Get get) {
