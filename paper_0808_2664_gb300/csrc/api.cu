@@ -150,15 +150,11 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     // shrinks it until they do): taller leaves mean fewer tree nodes (the
     // tree's work is about n / (2h) of the leaves') and a smaller n^3 share
     // in forming Q, at one leaf CTA per SM.
-    // FP32 leaves are cheap in arithmetic and latency-bound, so they keep
-    // 68 KB tiles (three 256-thread CTAs per SM) instead.
-    if (q->es == 8) {
-      h = smax / 8 / n / 32 * 32;
-      if (h > 1024) h = 1024;
-    } else {
-      h = 1;
-      while (h * 2 <= 68 * 1024 / 4 / n && h * 2 <= 1024) h *= 2;
-    }
+    // FP32 leaves stop at 512 rows: beyond that the shorter tree no longer
+    // pays for the longer serial leaf (measured at n = 64 and 128).
+    h = smax / (int64_t)q->es / n / 32 * 32;
+    const int64_t hcap = q->es == 8 ? 1024 : 512;
+    if (h > hcap) h = hcap;
     if (h < n) h = n;
   }
   if (h < n) return -4;
