@@ -22,12 +22,27 @@ __host__ __device__ inline size_t leaf_tile_region(int n, int ld, size_t elem) {
   return tile > tm ? tile : tm;
 }
 
+// Warp groups of a leaf CTA of nt threads: warp 0 (reflectors), the update
+// warps, and nt/128 warps for Z = Y^T Y.
+__host__ __device__ constexpr int leaf_z_warps(int nt) { return nt / 128; }
+__host__ __device__ constexpr int leaf_u_warps(int nt) { return nt / 32 - 1 - leaf_z_warps(nt); }
+// Partial-dot slots: the update warps' (one per thread, or one per column),
+// then two double-buffered pairs of slices for the Z warps.
+__host__ __device__ constexpr int leaf_upart(int nt) { return 32 * leaf_u_warps(nt) > 128 ? 32 * leaf_u_warps(nt) : 128; }
+__host__ __device__ constexpr int leaf_zslice(int nt) { return 32 * leaf_z_warps(nt) > 64 ? 32 * leaf_z_warps(nt) : 64; }
+__host__ __device__ constexpr int leaf_part_entries(int nt) { return leaf_upart(nt) + 4 * leaf_zslice(nt); }
+
 // Shared-memory bytes for a leaf of up to ld rows with NT threads: the tile
-// region, NT partial dots, two per-column coefficient vectors, and FP64
-// per-column scalars (tau, reflector scale) plus 32 per-warp partial norms.
+// region, the partial dots, two per-column coefficient vectors, and FP64
+// per-column scalars (tau, reflector scale, scaling exponent) plus 128
+// per-lane partial norms and the Z group's progress word.
 __host__ __device__ inline size_t leaf_smem_bytes(int n, int ld, size_t elem, int nt) {
-  return leaf_tile_region(n, ld, elem) + leaf_align_up(elem * 3 * (size_t)nt, 8) + 2 * leaf_align_up(elem * (size_t)n, 8) +
-         sizeof(double) * (3 * (size_t)n + 128);
+  return leaf_tile_region(n, ld, elem) + leaf_align_up(elem * (size_t)leaf_part_entries(nt), 8) +
+         2 * leaf_align_up(elem * (size_t)n, 8) + sizeof(double) * (3 * (size_t)n + 128 + 2);
+}
+
+__device__ __forceinline__ void leaf_named_barrier(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // Exponent k of the power of two 2^k that brings the largest magnitude of a
@@ -77,31 +92,36 @@ __device__ __forceinline__ int leaf_groups(int threads, int rows) {
 //       with that update, its partial dot with a_k's tail; meanwhile warp 0
 //       alone turns column k's (alpha, ||tail||^2) into (beta, tau_k, s_k);
 //   S1  w_c = a_c(k) + s_k (a_k(k+1:)^T a_c(k+1:)) and tau_k w_c per column;
-//   S2  column k + 1 alone receives H_k (four warps, one per SM
-//       sub-partition) and the squared norm of its tail is summed per warp,
+//   S2  column k + 1 alone receives H_k (up to four warps, one per SM
+//       sub-partition) and the squared norm of its tail is left per lane,
 //       ready for the next step's reflector.
-// Three barriers per column; the bulk of the arithmetic (update and dot) is
-// one pass over the trailing block.
+// Three barriers per column among these warps; the bulk of the arithmetic
+// (update and dot) is one pass over the trailing block.  A separate group
+// of warps takes the products for T's Z = Y^T Y column by column as the
+// tails become final, off those barriers (see the loop below).
 template <typename T, int NT, int NMAX>
 __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl, T* taul, T* Tg, int* status,
                                 unsigned char* smem) {
   static_assert(NT >= 128, "the leaf schedule needs at least four warps");
   T* S = reinterpret_cast<T*>(smem);
   unsigned char* aux = smem + leaf_tile_region(n, ld, sizeof(T));
-  T* part = reinterpret_cast<T*>(aux);  // 3 NT partial dots (update warps, then the two of each Z pair)
-  T* coef = reinterpret_cast<T*>(aux + leaf_align_up(sizeof(T) * 3 * NT, 8));  // n: tau_k w_c
+  constexpr int kUPart = leaf_upart(NT), kZSlice = leaf_zslice(NT);
+  T* part = reinterpret_cast<T*>(aux);  // update warps' partial dots
+  T* zpart = part + kUPart;             // Z warps': [parity][d1 | d2][kZSlice]
+  T* coef = reinterpret_cast<T*>(aux + leaf_align_up(sizeof(T) * leaf_part_entries(NT), 8));  // n: tau_k w_c
   T* cscl = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(coef) + leaf_align_up(sizeof(T) * n, 8));  // n: tau_k w_c s_k
   double* tau_s = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(cscl) + leaf_align_up(sizeof(T) * n, 8));
   double* sc_s = tau_s + n;  // n: reflector scales s_k
   int* cexp = reinterpret_cast<int*>(sc_s + n);  // n: column scaling exponents (n doubles reserved)
   double* wsum = sc_s + 2 * n;  // 128 per-lane partial squared norms (the S2 warps' lanes)
+  volatile int* zready = reinterpret_cast<volatile int*>(wsum + 128);  // columns whose tails are final
   T* Tm = reinterpret_cast<T*>(smem);  // n x n, after write-back
   T* Wt = Tm + (size_t)n * n;          // doubling workspace
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  constexpr int kWarps = NT / 32;
-  constexpr int kS2Warps = 4;           // warps of the single-column phase S2
-  constexpr int kPWarps = kWarps - 1;   // warps of phase P (all but warp 0)
+  constexpr int kUWarps = leaf_u_warps(NT), kZWarps = leaf_z_warps(NT);
+  constexpr int kMThreads = 32 * (1 + kUWarps), kZThreads = 32 * kZWarps;
+  constexpr int kS2Warps = 1 + kUWarps < 4 ? 1 + kUWarps : 4;  // warps of the single-column phase S2
 
   // Load the tile: each thread walks the column-major elements e = tid + t NT,
   // several loads in flight.
@@ -140,7 +160,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   }
   __syncthreads();
   // Largest magnitude of each column (one warp per column, integer maxima).
-  for (int c = warp; c < n; c += kWarps) {
+  for (int c = warp; c < n; c += NT / 32) {
     const T* col = S + c * ld;
     unsigned mx = 0u;
     for (int i = lane; i < hl; i += 32) {
@@ -172,50 +192,47 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   }
   __syncthreads();
 
-  // Z = strictly-upper(Y^T Y), needed for T, is taken inside the loop:
+  // Two warp groups run the column loop.  Group M (warp 0 and the update
+  // warps) carries the factorisation, with its own barrier.  Group Z takes
+  // the dots behind Z = strictly-upper(Y^T Y), needed for T:
   //   Z(p, q) = u_p^T u_q = s_p (a_p(q) + s_q a_p(q+1:)^T a_q(q+1:)),  p < q,
-  // as soon as a_q's tail is final (step q), in pairs (p, p+1) per work item.
-  // Its work grows with q while the update work shrinks, so the two together
-  // keep phase P large at every step.  Z goes to Tg (global, read back for T).
-  //
-  // Work items of phase P: (column, row group) for the updates, then, from
-  // the next warp boundary on, (pair, row group) for Z.  Every column or pair
-  // gets the same number rg <= kLeafMaxGroups of row groups: one or two
-  // warps per SM sub-partition already keep its FP64 pipe busy, and fewer
-  // partial sums shorten the reductions of S1, which no other work overlaps.
-  for (int k = 0; k < n; ++k) {
-    T* colk = S + k * ld;
-    const int acols = n - 1 - k;     // trailing columns k+1 .. n-1
-    const int npairs = (k + 1) / 2;  // Z pairs of column k
-    int rg = acols + npairs > 0 ? (32 * kPWarps) / (acols + npairs) : 1;
-    rg = leaf_groups(rg < kLeafMaxGroups ? rg : kLeafMaxGroups, hl - k);
-    const int nu = acols * rg;                // update items
-    const int zbase = (nu + 31) / 32 * 32;    // first Z item
-    const int nitems = zbase + npairs * rg;
-    if (warp == 0) {
-      // Reflector k, from alpha = a_k(k) and the per-lane squared norms of
-      // a_k's tail (summed by this warp, off the path of the other phases).
-      // Nothing else reads a_k(k) in this phase.
-      double ssq = (wsum[lane] + wsum[lane + 32]) + (wsum[lane + 64] + wsum[lane + 96]);
+  // the unscaled dot d(p, q) = a_p(q+1:)^T a_q(q+1:) as soon as M reports
+  // column q's tail final, in pairs (p, p+1) per work item, with its own
+  // barrier; d goes to Tg and is turned into Z after the loop.  Z's work
+  // (about a third of the products) thus fills the FP64 pipe while M waits
+  // in its serial per-column steps.
+  if (tid == 0) *zready = 0;
+  __syncthreads();
+  if (warp <= kUWarps) {
+    for (int k = 0; k < n; ++k) {
+      T* colk = S + k * ld;
+      const int acols = n - 1 - k;  // trailing columns k+1 .. n-1
+      int rg = acols > 0 ? (32 * kUWarps) / acols : 1;
+      rg = leaf_groups(rg < kLeafMaxGroups ? rg : kLeafMaxGroups, hl - k);
+      if (warp == 0) {
+        // Reflector k, from alpha = a_k(k) and the per-lane squared norms of
+        // a_k's tail.  Nothing else reads a_k(k) in this phase.
+        double ssq = 0.0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
-      if (lane == 0) {
-        const double alpha = (double)colk[k];
-        const int len = hl - k - 1;
-        Reflector r = make_reflector(
-            alpha, ssq, [&]() { return scaled_norm(len, [&](int i) { return (double)colk[k + 1 + i]; }); },
-            status);
-        tau_s[k] = r.tau;
-        sc_s[k] = r.scale;
-        colk[k] = (T)r.beta;
-      }
-      __syncwarp();
-    } else {
-      for (int item = tid - 32; item < nitems; item += 32 * kPWarps) {
-        if (item < nu) {
-          // Update item: H_{k-1} on column c and the partial dot with a_k's
-          // tail, rows interleaved over the rg groups (group g takes rows
-          // k-1+g, k-1+g+rg, ...).
+        for (int w = 0; w < kS2Warps; ++w) ssq += wsum[lane + 32 * w];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+        if (lane == 0) {
+          const double alpha = (double)colk[k];
+          const int len = hl - k - 1;
+          Reflector r = make_reflector_fast(
+              alpha, ssq, [&]() { return scaled_norm(len, [&](int i) { return (double)colk[k + 1 + i]; }); },
+              status);
+          tau_s[k] = r.tau;
+          sc_s[k] = r.scale;
+          colk[k] = (T)r.beta;
+        }
+        __syncwarp();
+      } else if (acols > 0) {
+        // P: H_{k-1} on column c and the partial dot with a_k's tail, rows
+        // interleaved over the rg groups (group g takes rows k-1+g,
+        // k-1+g+rg, ...).
+        for (int item = tid - 32; item < acols * rg; item += 32 * kUWarps) {
           const int slot = item % acols, g = item / acols;
           const int c = k + 1 + slot;
           T* cc = S + c * ld;
@@ -254,81 +271,107 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
             }
           }
           part[g * acols + slot] = s0 + s1;
-        } else if (item >= zbase) {
-          // Z item: partial dots of a_k's tail with a_p and a_p2.
-          const int zi = item - zbase;
-          const int t = zi % npairs, g = zi / npairs;
-          const int p = 2 * t, p2 = 2 * t + 1 < k ? 2 * t + 1 : 2 * t;
-          const T* x1 = S + p * ld;
-          const T* x2 = S + p2 * ld;
-          T z1 = T(0), z2 = T(0), z3 = T(0), z4 = T(0);
-          int i = k + 1 + g;
-          for (; i + rg < hl; i += 2 * rg) {
-            const T v0 = colk[i], v1 = colk[i + rg];
-            z1 = fma(v0, x1[i], z1);
-            z2 = fma(v0, x2[i], z2);
-            z3 = fma(v1, x1[i + rg], z3);
-            z4 = fma(v1, x2[i + rg], z4);
-          }
-          if (i < hl) {
-            z1 = fma(colk[i], x1[i], z1);
-            z2 = fma(colk[i], x2[i], z2);
-          }
-          part[NT + g * npairs + t] = z1 + z3;
-          part[2 * NT + g * npairs + t] = z2 + z4;
         }
       }
-    }
-    __syncthreads();
-    // S1: coefficients of H_k for the trailing columns (threads 0..acols-1),
-    // and the Z entries of column k (threads from the next warp boundary on,
-    // so that no warp does both).
-    {
-      const int zs1 = (acols + 31) / 32 * 32;
-      for (int sl = tid; sl < zs1 + npairs; sl += NT) {
-        if (sl < acols) {
-          T d0 = T(0), d1 = T(0);
-          int gg = 0;
-          for (; gg + 1 < rg; gg += 2) {
-            d0 += part[gg * acols + sl];
-            d1 += part[(gg + 1) * acols + sl];
-          }
-          if (gg < rg) d0 += part[gg * acols + sl];
-          const int cidx = k + 1 + sl;
-          const double tk = tau_s[k], sk = sc_s[k], ts = tk * sk;
-          const double w = fma(sk, (double)(d0 + d1), (double)S[cidx * ld + k]);
-          coef[cidx] = (T)(tk * w);
-          cscl[cidx] = (T)(ts * w);
-        } else if (sl >= zs1) {
-          const int t = sl - zs1;
-          T d1 = T(0), d2 = T(0);
-          for (int gg = 0; gg < rg; ++gg) {
-            d1 += part[NT + gg * npairs + t];
-            d2 += part[2 * NT + gg * npairs + t];
-          }
-          const int p = 2 * t, p2 = 2 * t + 1;
-          Tg[p + k * n] = (T)(sc_s[p] * ((double)S[p * ld + k] + sc_s[k] * (double)d1));
-          if (p2 < k) Tg[p2 + k * n] = (T)(sc_s[p2] * ((double)S[p2 * ld + k] + sc_s[k] * (double)d2));
+      leaf_named_barrier(1, kMThreads);
+      if (acols == 0) break;
+      // S1: coefficients of H_k for the trailing columns.
+      if (tid < acols) {
+        T d0 = T(0), d1 = T(0);
+        int gg = 0;
+        for (; gg + 1 < rg; gg += 2) {
+          d0 += part[gg * acols + tid];
+          d1 += part[(gg + 1) * acols + tid];
         }
+        if (gg < rg) d0 += part[gg * acols + tid];
+        const int cidx = k + 1 + tid;
+        const double tk = tau_s[k], sk = sc_s[k], ts = tk * sk;
+        const double w = fma(sk, (double)(d0 + d1), (double)S[cidx * ld + k]);
+        coef[cidx] = (T)(tk * w);
+        cscl[cidx] = (T)(ts * w);
+      }
+      leaf_named_barrier(1, kMThreads);
+      // S2: column k+1 receives H_k; squared norm of its tail below row k+1.
+      if (warp < kS2Warps) {
+        T* ca = S + (k + 1) * ld;
+        const T cf = coef[k + 1], cs = cscl[k + 1];
+        double ss = 0.0;
+        if (tid == 0) ca[k] -= cf;
+        for (int i = k + 1 + tid; i < hl; i += 32 * kS2Warps) {
+          const T a = fma(-cs, colk[i], ca[i]);
+          ca[i] = a;
+          if (i > k + 1) ss = fma((double)a, (double)a, ss);
+        }
+        wsum[tid] = ss;
+      }
+      leaf_named_barrier(1, kMThreads);
+      if (tid == 0) {
+        __threadfence_block();
+        *zready = k + 1;  // column k+1's tail is final
       }
     }
-    __syncthreads();
-    if (acols == 0) break;
-    // S2: column k+1 receives H_k; squared norm of its tail below row k+1.
-    if (warp < kS2Warps) {
-      T* ca = S + (k + 1) * ld;
-      const T cf = coef[k + 1], cs = cscl[k + 1];
-      double ss = 0.0;
-      if (tid == 0) ca[k] -= cf;
-      for (int i = k + 1 + tid; i < hl; i += 32 * kS2Warps) {
-        const T a = fma(-cs, colk[i], ca[i]);
-        ca[i] = a;
-        if (i > k + 1) ss = fma((double)a, (double)a, ss);
+  } else {
+    const int ztid = tid - kMThreads;
+    bool wait_ok = true;
+    for (int q = 1; q < n; ++q) {
+      if (lane == 0 && wait_ok) {
+        int spins = 0;
+        while (*zready < q) {
+          if (++spins > (1 << 22)) {  // the update warps stopped reporting: give up, flag it
+            atomicOr(status, kStatusTimeout);
+            wait_ok = false;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence_block();
       }
-      wsum[tid] = ss;
+      __syncwarp();
+      const int npairs = (q + 1) / 2;
+      int rgz = kZThreads / npairs;
+      rgz = leaf_groups(rgz < kLeafMaxGroups ? rgz : kLeafMaxGroups, hl - q);
+      T* zp = zpart + (q & 1) * 2 * kZSlice;
+      const T* xq = S + q * ld;
+      for (int item = ztid; item < npairs * rgz; item += kZThreads) {
+        const int t = item % npairs, g = item / npairs;
+        const int p = 2 * t, p2 = 2 * t + 1 < q ? 2 * t + 1 : 2 * t;
+        const T* x1 = S + p * ld;
+        const T* x2 = S + p2 * ld;
+        T z1 = T(0), z2 = T(0), z3 = T(0), z4 = T(0);
+        int i = q + 1 + g;
+        for (; i + rgz < hl; i += 2 * rgz) {
+          const T v0 = xq[i], v1 = xq[i + rgz];
+          z1 = fma(v0, x1[i], z1);
+          z2 = fma(v0, x2[i], z2);
+          z3 = fma(v1, x1[i + rgz], z3);
+          z4 = fma(v1, x2[i + rgz], z4);
+        }
+        if (i < hl) {
+          z1 = fma(xq[i], x1[i], z1);
+          z2 = fma(xq[i], x2[i], z2);
+        }
+        zp[g * npairs + t] = z1 + z3;
+        zp[kZSlice + g * npairs + t] = z2 + z4;
+      }
+      leaf_named_barrier(2, kZThreads);
+      for (int t = ztid; t < npairs; t += kZThreads) {
+        T d1 = T(0), d2 = T(0);
+        for (int g = 0; g < rgz; ++g) {
+          d1 += zp[g * npairs + t];
+          d2 += zp[kZSlice + g * npairs + t];
+        }
+        Tg[2 * t + q * n] = d1;
+        if (2 * t + 1 < q) Tg[2 * t + 1 + q * n] = d2;
+      }
     }
-    __syncthreads();
   }
+  __syncthreads();
+  // Z(p, q) = s_p (a_p(q) + s_q d(p, q)) from the unscaled tails.
+  for (int idx = tid; idx < n * n; idx += NT) {
+    const int p = idx % n, q = idx / n;
+    if (p < q) Tg[idx] = (T)(sc_s[p] * ((double)S[p * ld + q] + sc_s[q] * (double)Tg[idx]));
+  }
+  __syncthreads();
   // Final values in the tile: Householder vectors u_k = s_k a_k below the
   // diagonal, and R with the column factors taken back out (on and above).
   for (int c = 0; c < n; ++c) {

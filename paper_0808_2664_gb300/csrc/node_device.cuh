@@ -80,7 +80,7 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
       double scale = 0.0;
       if (tid == 0) {
         const double alpha = (double)at(0, j, j);
-        Reflector r = make_reflector(
+        Reflector r = make_reflector_fast(
             alpha, ssq,
             [&]() { return scaled_norm(tail, [&](int v) { return (double)at(1 + v / jr, j, v % jr); }); }, status);
         tau_s[j] = r.tau;
