@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--m", type=int, default=4194304)
     p.add_argument("--n", type=int, default=64)
     p.add_argument("--leaf-rows", type=int, default=0, help="0 = the library default")
-    p.add_argument("--arity", type=int, default=2)
+    p.add_argument("--arity", type=int, default=0, help="0 = the library default")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -526,7 +526,7 @@ def ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args), leaves=nl, levels=info["levels"]),
+            "config": dict(workload_config(args), leaves=nl, levels=info["levels"], leaf_rows=h, arity=info["arity"]),
             "backward_error": r["berr"], "orthogonality": r["orth"],
             "tolerance": 10 * n * 2.0 ** -52 * m ** 0.5, "device_status": r["status"],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -174,7 +174,14 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
   }
   q->h = h;
   q->nleaves = nl;
-  q->q = opts && opts->arity > 0 ? opts->arity : 2;
+  // Default arity 4 where the four-triangle node fits in shared memory: per
+  // eliminated triangle it needs a third less work for T and for applying
+  // the node's Q than a binary node, and half the levels.
+  if (opts && opts->arity > 0) {
+    q->q = opts->arity;
+  } else {
+    q->q = (int64_t)node_factor_smem((int)n, 4, q->es) <= smax && (int64_t)node_apply_smem((int)n, 4, q->es) <= smax ? 4 : 2;
+  }
   if (q->q < 2 || q->q > 16) return -4;
   q->items.assign(1, nl);
   while (q->items.back() > 1) q->items.push_back((q->items.back() + q->q - 1) / q->q);

@@ -1,12 +1,13 @@
-// Binary tree-node QR of stacked triangles, G nodes per CTA in lock step.
+// Tree-node QR of Q stacked triangles, G nodes per CTA in lock step.
 //
-// A node factors [R_0; R_1] (two upper-triangular n x n children) with
-// structured Householder QR (Section 2.1, Eqs. TSQR_binarytree_2/_3, and the
-// remark on structured local QR): reflector k touches row k of R_0 and rows
-// 0..k of R_1, so its vector is e_k on top and an upper-triangular column
-// y_k below; nothing below the triangles is stored or touched (2n^3/3 flops
-// per node, Section 2.2).  The node's Y is the upper triangle that replaced
-// R_1.
+// A node factors [R_0; R_1; ...; R_{Q-1}] (upper-triangular n x n children)
+// with structured Householder QR (Section 2.1, Eqs. TSQR_binarytree_2/_3,
+// and the remark on structured local QR): reflector k touches row k of R_0
+// and rows 0..k of every other triangle, so its vector is e_k on top and an
+// upper-triangular column below in each lower block; nothing below the
+// triangles is stored or touched (2n^3/3 flops per eliminated triangle,
+// Section 2.2).  The node's Y is the Q-1 upper triangles that replaced
+// R_1..R_{Q-1}.
 //
 // A node has little work per column (at most n^2/2 products) behind a
 // serial chain per column (reflector, coefficients), so this kernel
@@ -45,15 +46,15 @@ __host__ __device__ inline size_t node2_t_bytes(int n, size_t elem) {
   return leaf_align_up(elem * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
 }
 
-// The region holding G nodes' packed triangles, reused for the T builds.
-__host__ __device__ inline size_t node2_region_bytes(int n, int G, size_t elem) {
-  const size_t data = leaf_align_up(elem * 2 * (size_t)G * node2_packed(n), 16);
+// The region holding G nodes' q packed triangles each, reused for the T builds.
+__host__ __device__ inline size_t node2_region_bytes(int n, int G, size_t elem, int q) {
+  const size_t data = leaf_align_up(elem * (size_t)q * G * node2_packed(n), 16);
   const size_t tb = node2_t_bytes(n, elem);
   return data > tb ? data : tb;
 }
 
-__host__ __device__ inline size_t node2_smem_bytes(int n, int G, size_t elem, int nt) {
-  return node2_region_bytes(n, G, elem) + leaf_align_up(elem * 3 * (size_t)nt, 8) +
+__host__ __device__ inline size_t node2_smem_bytes(int n, int G, size_t elem, int nt, int q) {
+  return node2_region_bytes(n, G, elem, q) + leaf_align_up(elem * 3 * (size_t)nt, 8) +
          2 * leaf_align_up(elem * (size_t)G * n, 8) + sizeof(double) * (3 * (size_t)G * n + 32);
 }
 
@@ -111,19 +112,19 @@ __device__ __forceinline__ void build_t_doubling_batch(T* base, size_t stride, i
   }
 }
 
-// Factors nodes node0 .. node0+G-1 of a binary tree level: children
-// Rin[2 node], Rin[2 node + 1] (n x n, ld n, upper part read with
-// L1-bypassing loads; a missing second child reads as zeros, which gives
-// tau = 0, Y = 0 and R = the lone child), outputs as node_factor_one with
-// kBuildT: R (Ro), Y (one n x n block), tau and T.  Nodes at or past `nodes`
-// are computed on zeros and not written.  Every thread of the block calls it.
-template <typename T, int NT, int G>
+// Factors nodes node0 .. node0+G-1 of a tree level of arity Q: children
+// Rin[Q node + b], b < Q (n x n, ld n, upper part read with L1-bypassing
+// loads; missing children read as zeros, which leave the others' R and give
+// zero reflector parts), outputs as node_factor_one with kBuildT: R (Ro),
+// Y (Q-1 blocks of n x n), tau and T.  Nodes at or past `nodes` are computed
+// on zeros and not written.  Every thread of the block calls it.
+template <typename T, int NT, int G, int Q>
 __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64_t nodes, int64_t node0, int n,
                                    T* Rout, T* Yout, T* Tout, T* tauout, int* status, unsigned char* smem) {
   static_assert(NT / 32 >= G + 2, "need a reflector warp, one column warp per node and a Z warp");
   const int pk = node2_packed(n);
   T* D = reinterpret_cast<T*>(smem);
-  unsigned char* aux = smem + node2_region_bytes(n, G, sizeof(T));
+  unsigned char* aux = smem + node2_region_bytes(n, G, sizeof(T), Q);
   T* part = reinterpret_cast<T*>(aux);  // 3 NT partial dots
   T* coef = reinterpret_cast<T*>(aux + leaf_align_up(sizeof(T) * 3 * NT, 8));  // G n: tau_k w_c
   T* cscl = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(coef) + leaf_align_up(sizeof(T) * G * n, 8));
@@ -135,54 +136,56 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int kPWarps = NT / 32 - 1;
   const int64_t nn = (int64_t)n * n;
-  // Column c of block b (0: R_0, 1: R_1) of node g, rows 0..c.
-  auto col = [&](int g, int b, int c) -> T* { return D + (size_t)(2 * g + b) * pk + c * (c + 1) / 2; };
+  // Column c of block b (0: R_0, b: R_b) of node g, rows 0..c.
+  auto col = [&](int g, int b, int c) -> T* { return D + (size_t)(Q * g + b) * pk + c * (c + 1) / 2; };
 
-  // Load the children's upper triangles, one warp per (node, column): both
+  // Load the children's upper triangles, one warp per (node, column): the
   // triangles' column c (rows 0..c), its largest magnitude, its power-of-two
   // factor applied on the way into shared memory.
   for (int gc = warp; gc < G * n; gc += NT / 32) {
     const int g = gc / n, c = gc - g * n;
     const int64_t node = node0 + g;
-    const bool has0 = node < nodes, has1 = node < nodes && 2 * node + 1 < nin;
-    const T* src0 = Rin + (2 * node) * nn + (int64_t)c * n;
-    const T* src1 = src0 + nn;
-    T v0[kMaxN / 32], v1[kMaxN / 32];
+    T v[Q][kMaxN / 32];
     unsigned mx = 0u;
 #pragma unroll
-    for (int r = 0; r < kMaxN / 32; ++r) {
-      const int i = lane + 32 * r;
-      v0[r] = T(0);
-      v1[r] = T(0);
-      if (i <= c) {
-        if (has0) v0[r] = __ldcg(src0 + i);
-        if (has1) v1[r] = __ldcg(src1 + i);
-        const unsigned b0 = sizeof(T) == 8 ? (unsigned)__double2hiint((double)v0[r]) : __float_as_uint((float)v0[r]);
-        const unsigned b1 = sizeof(T) == 8 ? (unsigned)__double2hiint((double)v1[r]) : __float_as_uint((float)v1[r]);
-        const unsigned m0 = b0 & 0x7fffffffu, m1 = b1 & 0x7fffffffu;
-        mx = m0 > mx ? m0 : mx;
-        mx = m1 > mx ? m1 : mx;
+    for (int b = 0; b < Q; ++b) {
+      const int64_t child = (int64_t)Q * node + b;
+      const bool has = node < nodes && child < nin;
+      const T* src = Rin + child * nn + (int64_t)c * n;
+#pragma unroll
+      for (int r = 0; r < kMaxN / 32; ++r) {
+        const int i = lane + 32 * r;
+        v[b][r] = T(0);
+        if (i <= c) {
+          if (has) v[b][r] = __ldcg(src + i);
+          const unsigned bits = sizeof(T) == 8 ? (unsigned)__double2hiint((double)v[b][r]) : __float_as_uint((float)v[b][r]);
+          const unsigned m = bits & 0x7fffffffu;
+          mx = m > mx ? m : mx;
+        }
       }
     }
     mx = __reduce_max_sync(0xffffffffu, mx);
     const int ex = column_exp2<T>(mx);
     const T f = pow2_bits<T>(ex);
     if (lane == 0) cexp[gc] = ex;
-    T* d0 = col(g, 0, c);
-    T* d1 = col(g, 1, c);
 #pragma unroll
-    for (int r = 0; r < kMaxN / 32; ++r) {
-      const int i = lane + 32 * r;
-      if (i <= c) {
-        d0[i] = v0[r] * f;
-        d1[i] = v1[r] * f;
+    for (int b = 0; b < Q; ++b) {
+      T* d = col(g, b, c);
+#pragma unroll
+      for (int r = 0; r < kMaxN / 32; ++r) {
+        const int i = lane + 32 * r;
+        if (i <= c) d[i] = v[b][r] * f;
       }
     }
   }
   __syncthreads();
   if (tid < G) {
-    const double x = (double)col(tid, 1, 0)[0];
-    ssq[tid] = x * x;
+    double x2 = 0.0;
+    for (int b = 1; b < Q; ++b) {
+      const double x = (double)col(tid, b, 0)[0];
+      x2 = fma(x, x, x2);
+    }
+    ssq[tid] = x2;
   }
   __syncthreads();
 
@@ -202,14 +205,15 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
     const int zbase = (nu + 31) / 32 * 32;
     const int nitems = zbase + zcols * rg;
     if (warp == 0) {
-      // Reflector k of node g (lane g): alpha = R_0(k, k), tail = R_1(0..k, k).
+      // Reflector k of node g (lane g): alpha = R_0(k, k), tail = R_b(0..k, k), b >= 1.
       if (lane < G) {
         const int g = lane;
         T* ck0 = col(g, 0, k);
-        const T* ck1 = col(g, 1, k);
         const double alpha = (double)ck0[k];
         Reflector r = make_reflector_fast(
-            alpha, ssq[g], [&]() { return scaled_norm(k + 1, [&](int i) { return (double)ck1[i]; }); }, status);
+            alpha, ssq[g],
+            [&]() { return scaled_norm((Q - 1) * (k + 1), [&](int v) { return (double)col(g, 1 + v / (k + 1), k)[v % (k + 1)]; }); },
+            status);
         tau_s[g * n + k] = r.tau;
         sc_s[g * n + k] = r.scale;
         ck0[k] = (T)r.beta;
@@ -218,51 +222,60 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
     } else {
       for (int item = tid - 32; item < nitems; item += 32 * kPWarps) {
         if (item < nu) {
-          // H_{k-1} on trailing column c (R_0 row k-1; R_1 rows 0..k-1) fused
-          // with the partial dot of R_1 rows 0..k with column k's tail.
+          // H_{k-1} on trailing column c (R_0 row k-1; rows 0..k-1 of every
+          // lower block) fused with the partial dot of their rows 0..k with
+          // column k's tail.
           const int slot = item % ucols, grp = item / ucols;
           const int g = slot / acols, c = k + 1 + slot % acols;
-          T* cc1 = col(g, 1, c);
-          const T* ak = col(g, 1, k);
           T s0 = T(0), s1 = T(0);
           if (k == 0) {
-            if (grp == 0) s0 = ak[0] * cc1[0];
+            if (grp == 0)
+              for (int b = 1; b < Q; ++b) s0 = fma(col(g, b, 0)[0], col(g, b, c)[0], s0);
           } else {
-            const T* up = col(g, 1, k - 1);
             const T cf = coef[g * n + c], cs = cscl[g * n + c];
             if (grp == 0) col(g, 0, c)[k - 1] -= cf;  // the unit entry of u_{k-1}: R(k-1, c)
-            int i = grp;
-            for (; i + rg < k; i += 2 * rg) {
-              const T a0 = fma(-cs, up[i], cc1[i]);
-              const T a1 = fma(-cs, up[i + rg], cc1[i + rg]);
-              cc1[i] = a0;
-              cc1[i + rg] = a1;
-              s0 = fma(ak[i], a0, s0);
-              s1 = fma(ak[i + rg], a1, s1);
+#pragma unroll
+            for (int b = 1; b < Q; ++b) {
+              T* cc1 = col(g, b, c);
+              const T* ak = col(g, b, k);
+              const T* up = col(g, b, k - 1);
+              int i = grp;
+              for (; i + rg < k; i += 2 * rg) {
+                const T a0 = fma(-cs, up[i], cc1[i]);
+                const T a1 = fma(-cs, up[i + rg], cc1[i + rg]);
+                cc1[i] = a0;
+                cc1[i + rg] = a1;
+                s0 = fma(ak[i], a0, s0);
+                s1 = fma(ak[i + rg], a1, s1);
+              }
+              if (i < k) {
+                const T a0 = fma(-cs, up[i], cc1[i]);
+                cc1[i] = a0;
+                s0 = fma(ak[i], a0, s0);
+                i += rg;
+              }
+              if (i == k) s1 = fma(ak[k], cc1[k], s1);  // row k: not touched by H_{k-1}
             }
-            if (i < k) {
-              const T a0 = fma(-cs, up[i], cc1[i]);
-              cc1[i] = a0;
-              s0 = fma(ak[i], a0, s0);
-              i += rg;
-            }
-            if (i == k) s1 = fma(ak[k], cc1[k], s1);  // row k: not touched by H_{k-1}
           }
           part[grp * ucols + slot] = s0 + s1;
         } else if (item >= zbase) {
-          // Z(p, k) and Z(p2, k): partial dots of R_1 columns over rows 0..p(2).
+          // Z(p, k) and Z(p2, k): partial dots of the lower blocks' columns
+          // over rows 0..p(2).
           const int zi = item - zbase;
           const int slot = zi % zcols, grp = zi / zcols;
           const int g = slot / npairs, t = slot % npairs;
           const int p = 2 * t, p2 = 2 * t + 1 < k ? 2 * t + 1 : 2 * t;
-          const T* ak = col(g, 1, k);
-          const T* x1 = col(g, 1, p);
-          const T* x2 = col(g, 1, p2);
           T z1 = T(0), z2 = T(0);
-          for (int i = grp; i <= p2; i += rg) {
-            const T v = ak[i];
-            if (i <= p) z1 = fma(v, x1[i], z1);
-            z2 = fma(v, x2[i], z2);
+#pragma unroll
+          for (int b = 1; b < Q; ++b) {
+            const T* ak = col(g, b, k);
+            const T* x1 = col(g, b, p);
+            const T* x2 = col(g, b, p2);
+            for (int i = grp; i <= p2; i += rg) {
+              const T v = ak[i];
+              if (i <= p) z1 = fma(v, x1[i], z1);
+              z2 = fma(v, x2[i], z2);
+            }
           }
           part[NT + grp * zcols + slot] = z1;
           part[2 * NT + grp * zcols + slot] = z2;
@@ -301,17 +314,20 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
       if (acols > 0) {
         cf1 = __shfl_sync(0xffffffffu, cf1, 0);
         cs1 = __shfl_sync(0xffffffffu, cs1, 0);
-        T* cc1 = col(g, 1, k + 1);
-        const T* ak = col(g, 1, k);
         if (lane == 0) col(g, 0, k + 1)[k] -= cf1;
         double ss = 0.0;
-        for (int i = lane; i <= k + 1; i += 32) {
-          T v = cc1[i];
-          if (i <= k) {
-            v = fma(-cs1, ak[i], v);
-            cc1[i] = v;
+#pragma unroll
+        for (int b = 1; b < Q; ++b) {
+          T* cc1 = col(g, b, k + 1);
+          const T* ak = col(g, b, k);
+          for (int i = lane; i <= k + 1; i += 32) {
+            T v = cc1[i];
+            if (i <= k) {
+              v = fma(-cs1, ak[i], v);
+              cc1[i] = v;
+            }
+            ss = fma((double)v, (double)v, ss);
           }
-          ss = fma((double)v, (double)v, ss);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -339,7 +355,8 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
     if (acols == 0) break;
   }
   // Outputs, one warp per (node, column): R (column factors taken back
-  // out), Y = s_c * (R_1 column c), zeros below the diagonal; tau.
+  // out), Y_b = s_c * (R_b column c) for b >= 1, zeros below the diagonal;
+  // tau.
   for (int gc = warp; gc < G * n; gc += NT / 32) {
     const int g = gc / n, c = gc - g * n;
     const int64_t node = node0 + g;
@@ -347,12 +364,13 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
       const T fr = pow2_bits<T>(-cexp[gc]);
       const double sy = sc_s[gc];
       const T* r0 = col(g, 0, c);
-      const T* r1 = col(g, 1, c);
       T* ro = Rout + node * nn + (int64_t)c * n;
-      T* yo = Yout + node * nn + (int64_t)c * n;
-      for (int i = lane; i < n; i += 32) {
-        ro[i] = i <= c ? r0[i] * fr : T(0);
-        yo[i] = i <= c ? (T)((double)r1[i] * sy) : T(0);
+      for (int i = lane; i < n; i += 32) ro[i] = i <= c ? r0[i] * fr : T(0);
+#pragma unroll
+      for (int b = 1; b < Q; ++b) {
+        const T* rb = col(g, b, c);
+        T* yo = Yout + (node * (Q - 1) + (b - 1)) * nn + (int64_t)c * n;
+        for (int i = lane; i < n; i += 32) yo[i] = i <= c ? (T)((double)rb[i] * sy) : T(0);
       }
       if (lane == 0) tauout[node * n + c] = (T)tau_s[gc];
     }
@@ -361,7 +379,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
   // T of each node: Z (from Tout) above the diagonal, tau on it; as many
   // nodes at a time as the region holds.
   const size_t tstride = node2_t_bytes(n, sizeof(T)) / sizeof(T);
-  const int per_batch = (int)(node2_region_bytes(n, G, sizeof(T)) / node2_t_bytes(n, sizeof(T)));
+  const int per_batch = (int)(node2_region_bytes(n, G, sizeof(T), Q) / node2_t_bytes(n, sizeof(T)));
   for (int g0 = 0; g0 < G; g0 += per_batch) {
     const int cnt = G - g0 < per_batch ? G - g0 : per_batch;
     for (int gq = warp; gq < cnt * n; gq += NT / 32) {

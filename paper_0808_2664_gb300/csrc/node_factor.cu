@@ -36,18 +36,18 @@ __global__ void __launch_bounds__(NT) node_factor_kernel(NodeFactorArgs<T> a) {
 }
 
 // Binary levels: G nodes per CTA (node2_device.cuh), grid-stride over groups.
-template <typename T, int NT, int G>
+template <typename T, int NT, int G, int Q>
 __global__ void __launch_bounds__(NT) node2_factor_kernel(NodeFactorArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t groups = (a.nodes + G - 1) / G;
   for (int64_t gi = blockIdx.x; gi < groups; gi += gridDim.x)
-    node2_factor_group<T, NT, G>(a.Rin, a.nin, a.nodes, gi * G, a.n, a.Rout, a.Y, a.Tw, a.tau, a.status, smem);
+    node2_factor_group<T, NT, G, Q>(a.Rin, a.nin, a.nodes, gi * G, a.n, a.Rout, a.Y, a.Tw, a.tau, a.status, smem);
 }
 
-template <typename T, int NT, int G>
+template <typename T, int NT, int G, int Q>
 cudaError_t launch_node2(const NodeFactorArgs<T>& a, int sms, cudaStream_t s) {
-  const size_t smem = node2_smem_bytes(a.n, G, sizeof(T), NT);
-  auto kern = node2_factor_kernel<T, NT, G>;
+  const size_t smem = node2_smem_bytes(a.n, G, sizeof(T), NT, Q);
+  auto kern = node2_factor_kernel<T, NT, G, Q>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -62,22 +62,28 @@ cudaError_t launch_node2(const NodeFactorArgs<T>& a, int sms, cudaStream_t s) {
 
 }  // namespace
 
-size_t node2_factor_smem_max(int n, size_t elem) {
-  const size_t a = node2_smem_bytes(n, 1, elem, 256), b = node2_smem_bytes(n, 2, elem, 256);
-  return a > b ? a : b;
-}
+// Shared memory of the configuration launch_node_factor picks last (one
+// node per CTA), the smallest: the plan only has to know that one fits.
+size_t node2_factor_smem_min(int n, int q, size_t elem) { return node2_smem_bytes(n, 1, elem, 256, q); }
 
 template <typename T>
 cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
   if (a.nodes <= 0 || a.n <= 0) return cudaSuccess;
-  if (a.arity == 2) {
-    // Wide levels: two nodes per CTA share each serial step; narrow levels
-    // (fewer groups than about two per SM): one node per CTA, least latency.
-    int dev = 0, sms = 0;
+  if (a.arity == 2 || a.arity == 4) {
+    // Wide levels: two nodes per CTA share each serial step (when their
+    // tiles fit); narrow levels (fewer groups than about two per SM): one
+    // node per CTA, least latency.
+    int dev = 0, sms = 0, smax = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (a.nodes >= 4 * (int64_t)sms) return launch_node2<T, 256, 2>(a, sms, s);
-    return launch_node2<T, 256, 1>(a, sms, s);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool wide = a.nodes >= 4 * (int64_t)sms;
+    if (a.arity == 2) {
+      if (wide && node2_smem_bytes(a.n, 2, sizeof(T), 256, 2) <= (size_t)smax) return launch_node2<T, 256, 2, 2>(a, sms, s);
+      return launch_node2<T, 256, 1, 2>(a, sms, s);
+    }
+    if (wide && node2_smem_bytes(a.n, 2, sizeof(T), 256, 4) <= (size_t)smax) return launch_node2<T, 256, 2, 4>(a, sms, s);
+    return launch_node2<T, 256, 1, 4>(a, sms, s);
   }
   const size_t smem = node_smem_bytes(a.n, a.arity, sizeof(T), kNodeThreads);
   auto kern = node_factor_kernel<T, kNodeThreads>;
@@ -95,7 +101,7 @@ cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
 }
 
 size_t node_factor_smem(int n, int q, size_t elem) {
-  if (q == 2) return node2_factor_smem_max(n, elem);
+  if (q == 2 || q == 4) return node2_factor_smem_min(n, q, elem);
   return node_smem_bytes(n, q, elem, kNodeThreads);
 }
 
