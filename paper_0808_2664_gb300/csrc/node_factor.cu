@@ -70,19 +70,19 @@ template <typename T>
 cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
   if (a.nodes <= 0 || a.n <= 0) return cudaSuccess;
   if (a.arity == 2 || a.arity == 4) {
-    // Wide levels: two nodes per CTA share each serial step (when their
-    // tiles fit); narrow levels (fewer groups than about two per SM): one
-    // node per CTA, least latency.
+    // Binary wide levels: two nodes per CTA share each serial step (when
+    // their tiles fit); narrow binary levels (fewer groups than about two per
+    // SM) and arity 4: one node per CTA, three CTAs per SM at n = 64 (measured
+    // faster for the four-triangle nodes, whose steps are three times wider).
     int dev = 0, sms = 0, smax = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const bool wide = a.nodes >= 4 * (int64_t)sms;
     if (a.arity == 2) {
+      const bool wide = a.nodes >= 4 * (int64_t)sms;
       if (wide && node2_smem_bytes(a.n, 2, sizeof(T), 256, 2) <= (size_t)smax) return launch_node2<T, 256, 2, 2>(a, sms, s);
       return launch_node2<T, 256, 1, 2>(a, sms, s);
     }
-    if (wide && node2_smem_bytes(a.n, 2, sizeof(T), 256, 4) <= (size_t)smax) return launch_node2<T, 256, 2, 4>(a, sms, s);
     return launch_node2<T, 256, 1, 4>(a, sms, s);
   }
   const size_t smem = node_smem_bytes(a.n, a.arity, sizeof(T), kNodeThreads);
