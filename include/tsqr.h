@@ -126,6 +126,30 @@ int tsqr_apply_q(tsqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stre
 int tsqr_form_q(tsqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream);
 
 /*
+ * tsqr_factor_form_host: A = QR of a HOST matrix, with thin Q and R written
+ * back to HOST memory (Section 2.1: factor, then the Q factor with n
+ * columns), for data that lives on the host.  One call = tsqr_refactor +
+ * tsqr_form_q + the copies, pipelined: A goes to the device in chunks of
+ * leaves on a copy stream owned by the handle while the leaves already
+ * there are factored on `stream`; after the tree and the tree part of Q,
+ * Q comes back chunk by chunk as its leaves are formed.
+ *   A_host (m x n, column-major, lda_host >= m), read; Q_host (m x n,
+ *   ldq_host >= m) and R_host (n x n upper triangular, diag >= 0,
+ *   ldr_host >= n), written.  Page-locked host memory lets the copies
+ *   overlap the kernels; pageable memory works, without the overlap.
+ *   A, Q, R: device buffers of the same shapes (lda, ldq >= m, ldr >= n),
+ *   caller-owned; A ends holding the Householder vectors (the handle
+ *   borrows it, as after tsqr_refactor), Q the thin Q, R the R factor.
+ *   Q must not alias A.
+ * Asynchronous on `stream`: when `stream` reaches the end of the call, all
+ * host outputs are written.  Returns TSQR_OK, TSQR_ERR_HANDLE, -i for
+ * argument i (2..13) invalid, or a CUDA error code.
+ */
+int tsqr_factor_form_host(tsqr_q_t q, const void* A_host, int64_t lda_host, void* Q_host, int64_t ldq_host,
+                          void* R_host, int64_t ldr_host, void* A, int64_t lda, void* Q, int64_t ldq, void* R,
+                          int64_t ldr, tsqr_stream_t stream);
+
+/*
  * tsqr_sync_status: waits for the handle's work on `stream`, returns and
  * clears the latched device status (TSQR_OK, TSQR_ERR_NONFINITE, ...).
  */

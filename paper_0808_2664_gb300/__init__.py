@@ -44,12 +44,12 @@ def as_colmajor(t):
     return t.t().contiguous().t()
 
 
-def _ld(t, name: str) -> int:
+def _ld(t, name: str, host: bool = False) -> int:
     if t.dim() != 2:
         raise ValueError(f"{name} must be 2-D")
     m, n = t.shape
-    if not t.is_cuda:
-        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.is_cuda == host:
+        raise ValueError(f"{name} must be a {'host' if host else 'CUDA'} tensor")
     if n <= 1:
         if m > 1 and n == 1 and t.stride(0) != 1:
             raise ValueError(f"{name} must be column-major (unit row stride)")
@@ -138,6 +138,22 @@ class QTree:
         ldq = _ld(Q, "Q")
         check(lib().tsqr_form_q(self.ptr, ctypes.c_void_p(Q.data_ptr()), ldq, _stream(Q)), "tsqr_form_q")
         return Q
+
+    def factor_form_host(self, A_host, Q_host, R_host, A, Q, R):
+        """QR of a host matrix with Q and R written back to host memory, the copies pipelined
+        with the leaf work (tsqr_factor_form_host).  A_host, Q_host, R_host: column-major CPU
+        tensors (pinned for overlap); A, Q, R: device tensors of the same shapes.  Asynchronous
+        on the current stream of A's device."""
+        if tuple(A_host.shape) != (self.m, self.n) or A_host.dtype != self.dtype:
+            raise ValueError("A_host does not match the handle's shape / dtype")
+        check(lib().tsqr_factor_form_host(
+            self.ptr, ctypes.c_void_p(A_host.data_ptr()), _ld(A_host, "A_host", host=True),
+            ctypes.c_void_p(Q_host.data_ptr()), _ld(Q_host, "Q_host", host=True),
+            ctypes.c_void_p(R_host.data_ptr()), _ld(R_host, "R_host", host=True),
+            ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), ctypes.c_void_p(Q.data_ptr()), _ld(Q, "Q"),
+            ctypes.c_void_p(R.data_ptr()), _ld(R, "R"), _stream(A)), "tsqr_factor_form_host")
+        self.A = A
+        return Q_host, R_host
 
     STAGES = ("leaf_factor", "tree_factor", "leaf_apply", "tree_apply")
 

@@ -71,6 +71,11 @@ struct tsqr_q_s {
   int64_t launches[TSQR_NUM_STAGES] = {0, 0, 0, 0};
   // Arithmetic of the leaf-block Q^T products (CAQR trailing updates).
   int32_t upd = TSQR_PREC_FP64;
+  // Host pipeline (tsqr_factor_form_host): copy stream and per-chunk events,
+  // created on first use.
+  cudaStream_t copy = nullptr;
+  std::vector<cudaEvent_t> ev_in, ev_out;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
 };
 
 struct caqr_q_s {
@@ -244,24 +249,44 @@ int64_t slot_stride(const tsqr_q_s* q, int level) {
   return s;
 }
 
+// Rows [leaf_row0(l0), leaf_row0(l1)) hold leaves l0 .. l1-1; the last leaf
+// runs to m.
+int64_t leaf_row0(const tsqr_q_s* q, int64_t l) { return l >= q->nleaves ? q->m : l * q->h; }
+
+// Leaf QR of leaves [l0, l1) (the same kernel on a sub-range).
 template <typename T>
-cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
+cudaError_t launch_leaf_range(tsqr_q_s* q, T* A, int64_t lda, int64_t l0, int64_t l1, cudaStream_t s) {
+  const int64_t nn = q->n * q->n, r0 = leaf_row0(q, l0);
   LeafFactorArgs<T> la{};
-  la.A = A;
+  la.A = A + r0;
   la.lda = lda;
-  la.m = q->m;
+  la.m = leaf_row0(q, l1) - r0;
   la.n = (int)q->n;
   la.h = q->h;
-  la.nleaves = q->nleaves;
+  la.nleaves = l1 - l0;
   la.ld_s = leaf_factor_ld((int)q->hmax);
-  la.R = (T*)q->leafR;
-  la.tau = (T*)q->leafTau;
-  la.Tw = (T*)q->leafT;
+  la.R = (T*)q->leafR + l0 * nn;
+  la.tau = (T*)q->leafTau + l0 * q->n;
+  la.Tw = (T*)q->leafT + l0 * nn;
   la.status = q->status;
+  return launch_leaf_factor(la, s);
+}
+
+template <typename T>
+cudaError_t run_tree_factor(tsqr_q_s* q, T* R, int64_t ldr, bool zero_lower, cudaStream_t s);
+
+template <typename T>
+cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
   StageTimer t0(q, TSQR_STAGE_LEAF_FACTOR, s);
-  cudaError_t e = launch_leaf_factor(la, s);
+  cudaError_t e = launch_leaf_range(q, A, lda, 0, q->nleaves, s);
   if (e != cudaSuccess) return e;
   t0.stop(1);
+  return run_tree_factor(q, R, ldr, zero_lower, s);
+}
+
+template <typename T>
+cudaError_t run_tree_factor(tsqr_q_s* q, T* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   StageTimer t1(q, TSQR_STAGE_TREE_FACTOR, s);
   for (int l = 1; l <= q->levels; ++l) {
     NodeFactorArgs<T> na{};
@@ -283,20 +308,33 @@ cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool z
   return e;
 }
 
+// Leaf stage of Q C / Q^T C / form on leaves [l0, l1) (rows of C alike).
+template <typename T>
+LeafApplyArgs<T> leaf_apply_args(const tsqr_q_s* q, int64_t k, T* C, int64_t ldc, int64_t l0, int64_t l1) {
+  const int64_t r0 = leaf_row0(q, l0);
+  LeafApplyArgs<T> la{};
+  la.Y = (const T*)q->A + r0;
+  la.ldy = q->lda;
+  la.m = leaf_row0(q, l1) - r0;
+  la.n = (int)q->n;
+  la.h = q->h;
+  la.nleaves = l1 - l0;
+  la.Tw = (const T*)q->leafT + l0 * q->n * q->n;
+  la.C = C + r0;
+  la.ldc = ldc;
+  la.k = k;
+  return la;
+}
+
+// Tree stage of forming the thin Q: the root slot starts as diag(d), every
+// other row is produced top-down without being read.
+template <typename T>
+cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s);
+
 template <typename T>
 cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  LeafApplyArgs<T> la{};
-  la.Y = (const T*)q->A;
-  la.ldy = q->lda;
-  la.m = q->m;
-  la.n = (int)q->n;
-  la.h = q->h;
-  la.nleaves = q->nleaves;
-  la.Tw = (const T*)q->leafT;
-  la.C = C;
-  la.ldc = ldc;
-  la.k = k;
+  LeafApplyArgs<T> la = leaf_apply_args(q, k, C, ldc, 0, q->nleaves);
   auto node = [&](int l, int md) {
     NodeApplyArgs<T> na{};
     na.Y = (const T*)q->nodeY[l - 1];
@@ -346,16 +384,108 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
     }
     return leaf(kApplyQ);
   }
-  // Form the thin Q: the root slot starts as diag(d), every other row is
-  // produced top-down without being read.
-  {
-    StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
-    if ((e = launch_init_form(C, ldc, (int)q->n, (const T*)q->d, s)) != cudaSuccess) return e;
-    for (int l = q->levels; l >= 1; --l)
-      if ((e = node(l, kApplyForm)) != cudaSuccess) return e;
-    t.stop(q->levels + 1);
-  }
+  if ((e = run_tree_form(q, C, ldc, s)) != cudaSuccess) return e;
   return leaf(kApplyForm);
+}
+
+template <typename T>
+cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
+  if ((e = launch_init_form(C, ldc, (int)q->n, (const T*)q->d, s)) != cudaSuccess) return e;
+  for (int l = q->levels; l >= 1; --l) {
+    NodeApplyArgs<T> na{};
+    na.Y = (const T*)q->nodeY[l - 1];
+    na.Tw = (const T*)q->nodeT[l - 1];
+    na.nin = q->items[l - 1];
+    na.arity = q->q;
+    na.n = (int)q->n;
+    na.nodes = q->items[l];
+    na.slot_stride = slot_stride(q, l);
+    na.C = C;
+    na.ldc = ldc;
+    na.k = q->n;
+    na.mode = kApplyForm;
+    if ((e = launch_node_apply(na, s)) != cudaSuccess) return e;
+  }
+  t.stop(q->levels + 1);
+  return e;
+}
+
+// Host-buffer pipeline: A arrives in chunks of leaves on the copy stream
+// while the compute stream factors the chunks already in; the tree and the
+// tree part of forming Q follow; then Q leaves the device chunk by chunk
+// as the form finishes each one.  Chunks are whole waves of leaf CTAs.
+template <typename T>
+cudaError_t run_factor_form_host(tsqr_q_s* q, const T* Ah, int64_t ldah, T* Qh, int64_t ldqh, T* Rh, int64_t ldrh,
+                                 T* A, int64_t lda, T* Q, int64_t ldq, T* R, int64_t ldr, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  int64_t chunk = 4 * (int64_t)sms;  // four waves of one-CTA-per-SM leaves
+  if (chunk > q->nleaves) chunk = q->nleaves;
+  const int64_t nchunks = (q->nleaves + chunk - 1) / chunk;
+  if (!q->copy && (e = cudaStreamCreateWithFlags(&q->copy, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if (!q->ev_start && (e = cudaEventCreateWithFlags(&q->ev_start, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if (!q->ev_done && (e = cudaEventCreateWithFlags(&q->ev_done, cudaEventDisableTiming)) != cudaSuccess) return e;
+  while ((int64_t)q->ev_in.size() < nchunks) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if ((e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming)) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return e;
+    }
+    q->ev_in.push_back(a);
+    q->ev_out.push_back(b);
+  }
+  const size_t es = sizeof(T);
+  // The copy stream starts after everything already queued on s.
+  if ((e = cudaEventRecord(q->ev_start, s)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(q->copy, q->ev_start, 0)) != cudaSuccess) return e;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int64_t l0 = c * chunk, l1 = l0 + chunk < q->nleaves ? l0 + chunk : q->nleaves;
+    const int64_t r0 = leaf_row0(q, l0), r1 = leaf_row0(q, l1);
+    if ((e = cudaMemcpy2DAsync(A + r0, lda * es, Ah + r0, ldah * es, (r1 - r0) * es, q->n, cudaMemcpyHostToDevice,
+                               q->copy)) != cudaSuccess)
+      return e;
+    if ((e = cudaEventRecord(q->ev_in[c], q->copy)) != cudaSuccess) return e;
+  }
+  {
+    StageTimer t0(q, TSQR_STAGE_LEAF_FACTOR, s);
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int64_t l0 = c * chunk, l1 = l0 + chunk < q->nleaves ? l0 + chunk : q->nleaves;
+      if ((e = cudaStreamWaitEvent(s, q->ev_in[c], 0)) != cudaSuccess) return e;
+      if ((e = launch_leaf_range(q, A, lda, l0, l1, s)) != cudaSuccess) return e;
+    }
+    t0.stop(nchunks);
+  }
+  if ((e = run_tree_factor(q, R, ldr, true, s)) != cudaSuccess) return e;
+  q->A = A;
+  q->lda = lda;
+  q->factored = true;
+  if ((e = cudaMemcpy2DAsync(Rh, ldrh * es, R, ldr * es, q->n * es, q->n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return e;
+  if ((e = run_tree_form(q, Q, ldq, s)) != cudaSuccess) return e;
+  {
+    StageTimer t(q, TSQR_STAGE_LEAF_APPLY, s);
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int64_t l0 = c * chunk, l1 = l0 + chunk < q->nleaves ? l0 + chunk : q->nleaves;
+      LeafApplyArgs<T> la = leaf_apply_args(q, q->n, Q, ldq, l0, l1);
+      la.mode = kApplyForm;
+      if ((e = launch_leaf_apply(la, s)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(q->ev_out[c], s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(q->copy, q->ev_out[c], 0)) != cudaSuccess) return e;
+      const int64_t r0 = leaf_row0(q, l0), r1 = leaf_row0(q, l1);
+      if ((e = cudaMemcpy2DAsync(Qh + r0, ldqh * es, Q + r0, ldq * es, (r1 - r0) * es, q->n, cudaMemcpyDeviceToHost,
+                                 q->copy)) != cudaSuccess)
+        return e;
+    }
+    t.stop(nchunks);
+  }
+  // The call is complete on s once the last copy is.
+  if ((e = cudaEventRecord(q->ev_done, q->copy)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s, q->ev_done, 0);
 }
 
 int create_handle(int64_t m, int64_t n, int32_t prec, const tsqr_opts_t* opts, tsqr_q_t* out, unsigned char* external,
@@ -408,6 +538,13 @@ int destroy_handle(tsqr_q_s* q) {
   cudaError_t e = cudaSuccess;
   if (q->owns_ws && q->ws) e = cudaFree(q->ws);
   clear_events(q);
+  for (size_t i = 0; i < q->ev_in.size(); ++i) {
+    cudaEventDestroy(q->ev_in[i]);
+    cudaEventDestroy(q->ev_out[i]);
+  }
+  if (q->ev_start) cudaEventDestroy(q->ev_start);
+  if (q->ev_done) cudaEventDestroy(q->ev_done);
+  if (q->copy) cudaStreamDestroy(q->copy);
   delete q;
   return cuda_err(e);
 }
@@ -506,6 +643,34 @@ int tsqr_form_q(tsqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream) {
   if (Q == q->A) return -2;
   cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, kApplyForm, q->n, (double*)Q, ldq, (cudaStream_t)stream)
                                             : run_apply<float>(q, kApplyForm, q->n, (float*)Q, ldq, (cudaStream_t)stream);
+  return cuda_err(e);
+}
+
+int tsqr_factor_form_host(tsqr_q_t q, const void* A_host, int64_t lda_host, void* Q_host, int64_t ldq_host,
+                          void* R_host, int64_t ldr_host, void* A, int64_t lda, void* Q, int64_t ldq, void* R,
+                          int64_t ldr, tsqr_stream_t stream) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  const int64_t m = q->m, n = q->n;
+  if (!A_host) return -2;
+  if (lda_host < m) return -3;
+  if (!Q_host) return -4;
+  if (ldq_host < m) return -5;
+  if (!R_host) return -6;
+  if (ldr_host < n) return -7;
+  if (!A) return -8;
+  if (lda < m) return -9;
+  if (!Q || Q == A) return -10;
+  if (ldq < m) return -11;
+  if (!R) return -12;
+  if (ldr < n) return -13;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = q->prec == TSQR_PREC_FP64
+                      ? run_factor_form_host<double>(q, (const double*)A_host, lda_host, (double*)Q_host, ldq_host,
+                                                     (double*)R_host, ldr_host, (double*)A, lda, (double*)Q, ldq,
+                                                     (double*)R, ldr, s)
+                      : run_factor_form_host<float>(q, (const float*)A_host, lda_host, (float*)Q_host, ldq_host,
+                                                    (float*)R_host, ldr_host, (float*)A, lda, (float*)Q, ldq,
+                                                    (float*)R, ldr, s);
   return cuda_err(e);
 }
 

@@ -230,3 +230,28 @@ def test_plan_once_refactor_matches():
         assert np.array_equal(host(R), host(R_ref))
         Q = host(q.form_q())
         assert np.linalg.norm(A - Q @ host(R)) / np.linalg.norm(A) <= fp64_tol(m, n)
+
+
+@pytest.mark.parametrize("m,n,h", [(100_000, 8, 32), (50_000, 16, 64), (3000, 32, 256)])
+def test_factor_form_host_pipeline(oracle_mod, m, n, h):
+    """Host-buffer call (chunked copies overlapped with the leaves) equals the device calls bitwise
+    and the oracle within the bound; several chunks of leaves and a merged last leaf."""
+    A = inputs.gaussian(m, n, 21)
+    q = tq.tsqr_q_create(m, n, torch.float64, "cuda", leaf_rows=h)
+    Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    Ah.copy_(torch.from_numpy(A))
+    Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    Ad, Qd, Rd = tq.colmajor(m, n, torch.float64), tq.colmajor(m, n, torch.float64), tq.colmajor(n, n, torch.float64)
+    q.factor_form_host(Ah, Qh, Rh, Ad, Qd, Rd)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    R1, q1 = tq.tsqr_factor(dev(A), leaf_rows=h, arity=q.info()["arity"])
+    Q1 = q1.form_q()
+    assert torch.equal(Rh, R1.cpu()) and torch.equal(Qh, Q1.cpu())
+    Qo, Ro = oracle_mod.qr(A)
+    tol = fp64_tol(m, n) * np.linalg.cond(A)
+    assert np.linalg.norm(Rh.numpy() - Ro) / np.linalg.norm(Ro) <= tol
+    assert np.linalg.norm(Qh.numpy() - Qo) <= tol * n ** 0.5
+    q.destroy()
+    q1.destroy()
