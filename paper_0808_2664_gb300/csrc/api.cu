@@ -752,14 +752,13 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
       rc = TSQR_ERR_NOMEM;
       break;
     }
-    // Panels default to taller leaves than plain TSQR: the tree-node update
-    // work relative to the leaf update is n / (2h), and the panel factor
-    // is overlapped with the trailing update anyway.
+    // Panels take the plain TSQR default (the tallest leaf that fits): the
+    // tree part of each trailing update is about n / h of its leaf part.
+    // The BF16x3 update kernel stages at most kBf16x3MaxLeaf rows per leaf.
     tsqr_opts_t po = opts ? *opts : tsqr_opts_t{0, 0, 0};
-    if (po.leaf_rows == 0) {
+    if (po.leaf_rows == 0 && update_precision == TSQR_UPDATE_BF16X3) {
       int64_t h = 1;
-      const int64_t cap = update_precision == TSQR_UPDATE_BF16X3 ? kBf16x3MaxLeaf : 1024;
-      while (h * 2 <= (160 * 1024 / (int64_t)c->es) / jb && h * 2 <= cap) h *= 2;
+      while (h * 2 <= (160 * 1024 / (int64_t)c->es) / jb && h * 2 <= kBf16x3MaxLeaf) h *= 2;
       po.leaf_rows = h < jb ? jb : h;
     }
     rc = make_plan(p, m - j0, jb, c->prec, &po);
@@ -788,7 +787,15 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
     cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), s);
     if (e != cudaSuccess) rc = cuda_err(e);
   }
-  if (rc == TSQR_OK && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) rc = TSQR_ERR_CUDA;
+  // The look-ahead panel runs at the highest stream priority, so that its
+  // few leaf CTAs take SMs as the trailing update's CTAs retire instead of
+  // queueing behind the whole update.
+  if (rc == TSQR_OK) {
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi) != cudaSuccess)
+      rc = TSQR_ERR_CUDA;
+  }
   c->ev_left.assign(c->panels.size(), nullptr);
   c->ev_fact.assign(c->panels.size(), nullptr);
   for (size_t j = 0; j < c->panels.size() && rc == TSQR_OK; ++j) {
