@@ -25,6 +25,7 @@
 
 #include "../../include/tsqr.h"
 #include "leaf_device.cuh"
+#include "node2_device.cuh"
 #include "node_device.cuh"
 #include "tsqr_internal.cuh"
 
@@ -115,8 +116,9 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchArgs<T> a) {
     if (w.level == 0) {
       const int64_t r0 = w.idx * M.h;
       const int hl = (w.idx == M.nleaves - 1) ? (int)(M.m - r0) : (int)M.h;
-      leaf_factor_one<T, NT, kBatchNmax>(M.A + r0, M.lda, hl, n, M.ld_s, M.leafR + w.idx * nn,
-                                         M.leafTau + w.idx * (int64_t)n, M.leafT + w.idx * nn, a.status, smem);
+      // R only: no T for the leaves.
+      leaf_factor_one<T, NT, kBatchNmax, false>(M.A + r0, M.lda, hl, n, M.ld_s, M.leafR + w.idx * nn,
+                                                M.leafTau + w.idx * (int64_t)n, nullptr, a.status, smem);
       done_r = M.leafR + w.idx * nn;
     } else {
       const BLevel<T> L = a.levels[M.lvl0 + w.level - 1];
@@ -141,9 +143,18 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchArgs<T> a) {
       }
       __syncthreads();
       if (sh_ok) {
-        node_factor_one<T, NT, false>(Rin + c0 * nn, nc, M.q, n, L.R + w.idx * nn,
-                                      L.Y + w.idx * (int64_t)(M.q - 1) * nn, nullptr, L.tau + w.idx * (int64_t)n,
-                                      a.status, smem);
+        // Arity 2 and 4: the lock-step node kernel with one node per CTA and
+        // no T; other arities: the general one.
+        if (M.q == 2)
+          node2_factor_group<T, NT, 1, 2, false>(Rin, nin, L.items, w.idx, n, L.R, L.Y, nullptr, L.tau, a.status,
+                                                 smem);
+        else if (M.q == 4)
+          node2_factor_group<T, NT, 1, 4, false>(Rin, nin, L.items, w.idx, n, L.R, L.Y, nullptr, L.tau, a.status,
+                                                 smem);
+        else
+          node_factor_one<T, NT, false>(Rin + c0 * nn, nc, M.q, n, L.R + w.idx * nn,
+                                        L.Y + w.idx * (int64_t)(M.q - 1) * nn, nullptr, L.tau + w.idx * (int64_t)n,
+                                        a.status, smem);
       }
       done_r = L.R + w.idx * nn;
     }
@@ -270,7 +281,9 @@ int build_batch(tsqr_batch_s* b, const int64_t* m, const int64_t* n, void* const
       ncounters += its[l];
       levels.push_back(L);
     }
-    if (M.levels > 0) smem = std::max(smem, node_smem_bytes((int)ni, b->arity, es, NT));
+    if (M.levels > 0)
+      smem = std::max(smem, b->arity == 2 || b->arity == 4 ? node2_smem_bytes((int)ni, 1, es, NT, b->arity)
+                                                           : node_smem_bytes((int)ni, b->arity, es, NT));
   }
   int dev = 0, smax = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -78,8 +78,10 @@ __device__ __forceinline__ int leaf_groups(int threads, int rows) {
 
 // Factors one leaf: rows Ag[0..hl) (column stride lda) of an n-column matrix,
 // in place (Y below the diagonal, R_i on and above); writes the leaf R (n x n,
-// ld n) to Rl, tau to taul and the compact-WY T (n x n) to Tg.  Every thread
-// of the block calls it; smem holds leaf_smem_bytes(n, ld, sizeof(T), NT).
+// ld n) to Rl, tau to taul and, when kWantT, the compact-WY T (n x n) to Tg
+// (callers that need only R pass kWantT = false: no Z work, no T, Tg
+// unused).  Every thread of the block calls it; smem holds
+// leaf_smem_bytes(n, ld, sizeof(T), NT).
 //
 // Schedule.  Each column is first multiplied by a power of two that brings
 // its largest entry to [1/2, 1): Householder QR commutes exactly with such
@@ -99,7 +101,7 @@ __device__ __forceinline__ int leaf_groups(int threads, int rows) {
 // (update and dot) is one pass over the trailing block.  A separate group
 // of warps takes the products for T's Z = Y^T Y column by column as the
 // tails become final, off those barriers (see the loop below).
-template <typename T, int NT, int NMAX>
+template <typename T, int NT, int NMAX, bool kWantT = true>
 __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl, T* taul, T* Tg, int* status,
                                 unsigned char* smem) {
   static_assert(NT >= 128, "the leaf schedule needs at least four warps");
@@ -119,7 +121,8 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   T* Wt = Tm + (size_t)n * n;          // doubling workspace
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  constexpr int kUWarps = leaf_u_warps(NT), kZWarps = leaf_z_warps(NT);
+  constexpr int kZWarps = kWantT ? leaf_z_warps(NT) : 0;
+  constexpr int kUWarps = NT / 32 - 1 - kZWarps;
   constexpr int kMThreads = 32 * (1 + kUWarps), kZThreads = 32 * kZWarps;
   constexpr int kS2Warps = 1 + kUWarps < 4 ? 1 + kUWarps : 4;  // warps of the single-column phase S2
 
@@ -310,7 +313,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
         *zready = k + 1;  // column k+1's tail is final
       }
     }
-  } else {
+  } else if constexpr (kWantT) {
     const int ztid = tid - kMThreads;
     bool wait_ok = true;
     for (int q = 1; q < n; ++q) {
@@ -367,7 +370,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   }
   __syncthreads();
   // Z(p, q) = s_p (a_p(q) + s_q d(p, q)) from the unscaled tails.
-  for (int idx = tid; idx < n * n; idx += NT) {
+  for (int idx = tid; kWantT && idx < n * n; idx += NT) {
     const int p = idx % n, q = idx / n;
     if (p < q) Tg[idx] = (T)(sc_s[p] * ((double)S[p * ld + q] + sc_s[q] * (double)Tg[idx]));
   }
@@ -396,15 +399,17 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   }
   for (int cc = tid; cc < n; cc += NT) taul[cc] = (T)tau_s[cc];
   __syncthreads();
-  // Tm = Z above the diagonal (from Tg), tau on it, zero below.
-  for (int idx = tid; idx < n * n; idx += NT) {
-    const int p = idx % n, q = idx / n;
-    Tm[idx] = p == q ? (T)tau_s[p] : (p < q ? Tg[idx] : T(0));
+  if constexpr (kWantT) {
+    // Tm = Z above the diagonal (from Tg), tau on it, zero below.
+    for (int idx = tid; idx < n * n; idx += NT) {
+      const int p = idx % n, q = idx / n;
+      Tm[idx] = p == q ? (T)tau_s[p] : (p < q ? Tg[idx] : T(0));
+    }
+    __syncthreads();
+    build_t_doubling(Tm, Wt, n);
+    for (int idx = tid; idx < n * n; idx += NT) Tg[idx] = Tm[idx];
+    __syncthreads();
   }
-  __syncthreads();
-  build_t_doubling(Tm, Wt, n);
-  for (int idx = tid; idx < n * n; idx += NT) Tg[idx] = Tm[idx];
-  __syncthreads();
 }
 
 }  // namespace tsqr

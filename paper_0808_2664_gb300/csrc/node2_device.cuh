@@ -116,9 +116,10 @@ __device__ __forceinline__ void build_t_doubling_batch(T* base, size_t stride, i
 // Rin[Q node + b], b < Q (n x n, ld n, upper part read with L1-bypassing
 // loads; missing children read as zeros, which leave the others' R and give
 // zero reflector parts), outputs as node_factor_one with kBuildT: R (Ro),
-// Y (Q-1 blocks of n x n), tau and T.  Nodes at or past `nodes` are computed
-// on zeros and not written.  Every thread of the block calls it.
-template <typename T, int NT, int G, int Q>
+// Y (Q-1 blocks of n x n), tau and, when kBuildT, T (without it Tout is
+// unused).  Nodes at or past `nodes` are computed on zeros and not written.
+// Every thread of the block calls it.
+template <typename T, int NT, int G, int Q, bool kBuildT = true>
 __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64_t nodes, int64_t node0, int n,
                                    T* Rout, T* Yout, T* Tout, T* tauout, int* status, unsigned char* smem) {
   static_assert(NT / 32 >= G + 2, "need a reflector warp, one column warp per node and a Z warp");
@@ -191,7 +192,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
 
   for (int k = 0; k < n; ++k) {
     const int acols = n - 1 - k;     // trailing columns k+1 .. n-1
-    const int npairs = (k + 1) / 2;  // Z pairs (p, p+1), p < k, of column k
+    const int npairs = kBuildT ? (k + 1) / 2 : 0;  // Z pairs (p, p+1), p < k, of column k
     int rg = (32 * kPWarps) / (G * (acols + npairs) > 0 ? G * (acols + npairs) : 1);
     {
       int byrows = (k + 1) / kNode2MinRows;
@@ -258,12 +259,14 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
             }
           }
           part[grp * ucols + slot] = s0 + s1;
-        } else if (item >= zbase) {
+        } else if (kBuildT && item >= zbase) {
           // Z(p, k) and Z(p2, k): partial dots of the lower blocks' columns
           // over rows 0..p(2).
           const int zi = item - zbase;
-          const int slot = zi % zcols, grp = zi / zcols;
-          const int g = slot / npairs, t = slot % npairs;
+          const int zc = zcols > 0 ? zcols : 1;
+          const int slot = zi % zc, grp = zi / zc;
+          const int np = npairs > 0 ? npairs : 1;
+          const int g = slot / np, t = slot % np;
           const int p = 2 * t, p2 = 2 * t + 1 < k ? 2 * t + 1 : 2 * t;
           T z1 = T(0), z2 = T(0);
 #pragma unroll
@@ -333,9 +336,10 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0) ssq[g] = ss;
       }
-    } else if (warp > G) {
+    } else if (kBuildT && warp > G) {
       for (int zs = tid - 32 * (G + 1); zs < zcols; zs += NT - 32 * (G + 1)) {
-        const int g = zs / npairs, t = zs % npairs;
+        const int np = npairs > 0 ? npairs : 1;
+        const int g = zs / np, t = zs % np;
         T d1 = T(0), d2 = T(0);
         for (int gg = 0; gg < rg; ++gg) {
           d1 += part[NT + gg * zcols + zs];
@@ -376,6 +380,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
     }
   }
   __syncthreads();
+  if constexpr (!kBuildT) return;
   // T of each node: Z (from Tout) above the diagonal, tau on it; as many
   // nodes at a time as the region holds.
   const size_t tstride = node2_t_bytes(n, sizeof(T)) / sizeof(T);
