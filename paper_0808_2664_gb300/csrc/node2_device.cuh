@@ -192,7 +192,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
 
   for (int k = 0; k < n; ++k) {
     const int acols = n - 1 - k;     // trailing columns k+1 .. n-1
-    const int npairs = kBuildT ? (k + 1) / 2 : 0;  // Z pairs (p, p+1), p < k, of column k
+    const int npairs = kBuildT ? (k + 1) / 2 : 0;  // Z pairs (p, k-1-p) of column k
     int rg = (32 * kPWarps) / (G * (acols + npairs) > 0 ? G * (acols + npairs) : 1);
     {
       int byrows = (k + 1) / kNode2MinRows;
@@ -260,24 +260,30 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
           }
           part[grp * ucols + slot] = s0 + s1;
         } else if (kBuildT && item >= zbase) {
-          // Z(p, k) and Z(p2, k): partial dots of the lower blocks' columns
-          // over rows 0..p(2).
+          // Z(p, k) and Z(p2, k) with p = t, p2 = k-1-t (one entry when they
+          // meet): partial dots of the lower blocks' columns over their rows
+          // 0..p and 0..p2.  Pairing a short column with a long one gives
+          // every item k+1 rows, walked as one sequence (rows of p, then
+          // rows of p2) so that the lanes of a warp run the same count.
           const int zi = item - zbase;
           const int zc = zcols > 0 ? zcols : 1;
           const int slot = zi % zc, grp = zi / zc;
           const int np = npairs > 0 ? npairs : 1;
           const int g = slot / np, t = slot % np;
-          const int p = 2 * t, p2 = 2 * t + 1 < k ? 2 * t + 1 : 2 * t;
+          const int p = t, p2 = k - 1 - t;
+          const int len = p2 > p ? p + p2 + 2 : p + 1;
           T z1 = T(0), z2 = T(0);
 #pragma unroll
           for (int b = 1; b < Q; ++b) {
             const T* ak = col(g, b, k);
             const T* x1 = col(g, b, p);
             const T* x2 = col(g, b, p2);
-            for (int i = grp; i <= p2; i += rg) {
-              const T v = ak[i];
-              if (i <= p) z1 = fma(v, x1[i], z1);
-              z2 = fma(v, x2[i], z2);
+            for (int v = grp; v < len; v += rg) {
+              const bool first = v <= p;
+              const int i = first ? v : v - p - 1;
+              const T acc = fma(ak[i], (first ? x1 : x2)[i], first ? z1 : z2);
+              z1 = first ? acc : z1;
+              z2 = first ? z2 : acc;
             }
           }
           part[NT + grp * zcols + slot] = z1;
@@ -348,10 +354,10 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
         const int64_t node = node0 + g;
         if (node < nodes) {
           T* Tg = Tout + node * nn;
-          const int p = 2 * t, p2 = 2 * t + 1;
+          const int p = t, p2 = k - 1 - t;
           const double sk = sc_s[g * n + k];
           Tg[p + k * n] = (T)(sc_s[g * n + p] * sk * (double)d1);
-          if (p2 < k) Tg[p2 + k * n] = (T)(sc_s[g * n + p2] * sk * (double)d2);
+          if (p2 > p) Tg[p2 + k * n] = (T)(sc_s[g * n + p2] * sk * (double)d2);
         }
       }
     }
