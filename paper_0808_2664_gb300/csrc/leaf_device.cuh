@@ -18,7 +18,7 @@ __host__ __device__ inline size_t leaf_align_up(size_t x, size_t a) { return (x 
 // matrix plus the doubling workspace (both in the storage type).
 __host__ __device__ inline size_t leaf_tile_region(int n, int ld, size_t elem) {
   const size_t tile = leaf_align_up(elem * (size_t)n * ld, 16);
-  const size_t tm = leaf_align_up(elem * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
+  const size_t tm = leaf_align_up(elem * ((size_t)n * t_ld(n) + t_work_elems(n)), 16);
   return tile > tm ? tile : tm;
 }
 
@@ -117,8 +117,8 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   int* cexp = reinterpret_cast<int*>(sc_s + n);  // n: column scaling exponents (n doubles reserved)
   double* wsum = sc_s + 2 * n;  // 128 per-lane partial squared norms (the S2 warps' lanes)
   volatile int* zready = reinterpret_cast<volatile int*>(wsum + 128);  // columns whose tails are final
-  T* Tm = reinterpret_cast<T*>(smem);  // n x n, after write-back
-  T* Wt = Tm + (size_t)n * n;          // doubling workspace
+  T* Tm = reinterpret_cast<T*>(smem);  // n x n (leading dimension t_ld(n)), after write-back
+  T* Wt = Tm + (size_t)n * t_ld(n);    // doubling workspace
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int kZWarps = kWantT ? leaf_z_warps(NT) : 0;
@@ -375,39 +375,63 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
     if (p < q) Tg[idx] = (T)(sc_s[p] * ((double)S[p * ld + q] + sc_s[q] * (double)Tg[idx]));
   }
   __syncthreads();
-  // Final values in the tile: Householder vectors u_k = s_k a_k below the
-  // diagonal, and R with the column factors taken back out (on and above).
-  for (int c = 0; c < n; ++c) {
-    T* col = S + c * ld;
-    const T fr = pow2_bits<T>(-cexp[c]);
-    const double sy = sc_s[c];
-    for (int i = tid; i < hl; i += NT) {
-      if (i <= c) col[i] = col[i] * fr;
-      else col[i] = sizeof(T) == 8 ? (T)((double)col[i] * sy) : col[i] * (T)sy;
+  // Write back the leaf in one pass over its elements (several loads in
+  // flight per thread): Householder vectors u_c = s_c a_c below the
+  // diagonal, R with the column factors taken out on and above it.
+  {
+    const int total = hl * n;
+    int c = tid / hl, i = tid - c * hl;
+    const int dc = NT / hl, di = NT - dc * hl;
+    auto final_value = [&](int cc, int ii) -> T {
+      const T v = S[cc * ld + ii];
+      if (ii <= cc) return v * pow2_bits<T>(-cexp[cc]);
+      return sizeof(T) == 8 ? (T)((double)v * sc_s[cc]) : v * (T)sc_s[cc];
+    };
+    int e = tid;
+    for (; e + 3 * NT < total; e += 4 * NT) {
+      T v[4];
+      int cs[4], is[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cs[u] = c;
+        is[u] = i;
+        v[u] = final_value(c, i);
+        c += dc;
+        i += di;
+        if (i >= hl) {
+          i -= hl;
+          ++c;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Ag[(int64_t)cs[u] * lda + is[u]] = v[u];
     }
-  }
-  __syncthreads();
-  // Write back Y (below the diagonal) and R_i (on and above) in place, the
-  // leaf R factor to the tree's level-0 items, and tau.
-  for (int cc = 0; cc < n; ++cc) {
-    T* dst = Ag + (int64_t)cc * lda;
-    for (int i = tid; i < hl; i += NT) dst[i] = S[cc * ld + i];
+    for (; e < total; e += NT) {
+      Ag[(int64_t)c * lda + i] = final_value(c, i);
+      c += dc;
+      i += di;
+      if (i >= hl) {
+        i -= hl;
+        ++c;
+      }
+    }
   }
   for (int idx = tid; idx < n * n; idx += NT) {
     const int i = idx % n, cc = idx / n;
-    Rl[idx] = i <= cc ? S[cc * ld + i] : T(0);
+    Rl[idx] = i <= cc ? S[cc * ld + i] * pow2_bits<T>(-cexp[cc]) : T(0);
   }
   for (int cc = tid; cc < n; cc += NT) taul[cc] = (T)tau_s[cc];
   __syncthreads();
   if constexpr (kWantT) {
     // Tm = Z above the diagonal (from Tg), tau on it, zero below.
+    const int L = t_ld(n);
     for (int idx = tid; idx < n * n; idx += NT) {
       const int p = idx % n, q = idx / n;
-      Tm[idx] = p == q ? (T)tau_s[p] : (p < q ? Tg[idx] : T(0));
+      Tm[p + q * L] = p == q ? (T)tau_s[p] : (p < q ? Tg[idx] : T(0));
     }
     __syncthreads();
     build_t_doubling(Tm, Wt, n);
-    for (int idx = tid; idx < n * n; idx += NT) Tg[idx] = Tm[idx];
+    for (int idx = tid; idx < n * n; idx += NT) Tg[idx] = Tm[idx % n + (idx / n) * L];
     __syncthreads();
   }
 }

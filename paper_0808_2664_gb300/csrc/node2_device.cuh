@@ -41,9 +41,10 @@ constexpr int kNode2MinRows = 4;    // rows per group at least
 
 __host__ __device__ inline int node2_packed(int n) { return n * (n + 1) / 2; }
 
-// Bytes of one node's compact-WY doubling workspace (T, then n^2/2 + 1).
+// Bytes of one node's compact-WY doubling area: T (leading dimension
+// t_ld(n)), then the doubling workspace.
 __host__ __device__ inline size_t node2_t_bytes(int n, size_t elem) {
-  return leaf_align_up(elem * ((size_t)n * n + (size_t)n * n / 2 + 1), 16);
+  return leaf_align_up(elem * ((size_t)n * t_ld(n) + t_work_elems(n)), 16);
 }
 
 // The region holding G nodes' q packed triangles each, reused for the T builds.
@@ -56,60 +57,6 @@ __host__ __device__ inline size_t node2_region_bytes(int n, int G, size_t elem, 
 __host__ __device__ inline size_t node2_smem_bytes(int n, int G, size_t elem, int nt, int q) {
   return node2_region_bytes(n, G, elem, q) + leaf_align_up(elem * 3 * (size_t)nt, 8) +
          2 * leaf_align_up(elem * (size_t)G * n, 8) + sizeof(double) * (3 * (size_t)G * n + 32);
-}
-
-// T for `count` nodes at once: Tm_g = base + g * stride holds tau on the
-// diagonal, Z above it and zeros below; Wt_g = Tm_g + n^2 is the workspace.
-// The same merges as build_t_doubling, with the work items of all nodes
-// spread over the block.
-template <typename T>
-__device__ __forceinline__ void build_t_doubling_batch(T* base, size_t stride, int count, int n) {
-  for (int b = 1; b < n; b *= 2) {
-    const int npairs = (n + 2 * b - 1) / (2 * b);
-    const int bb = b * b;
-    const int per = npairs * bb;
-    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
-      const int g = idx / per, r0 = idx - g * per;
-      const int pair = r0 / bb, rem = r0 % bb;
-      const int pl = rem % b, ql = rem / b;
-      const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
-      if (q >= n) continue;
-      const T* Tm = base + g * stride;
-      T* Wt = base + g * stride + (size_t)n * n;
-      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-      int r = s + b;
-      for (; r + 3 <= q; r += 4) {
-        a0 = fma(Tm[p + r * n], Tm[r + q * n], a0);
-        a1 = fma(Tm[p + (r + 1) * n], Tm[r + 1 + q * n], a1);
-        a2 = fma(Tm[p + (r + 2) * n], Tm[r + 2 + q * n], a2);
-        a3 = fma(Tm[p + (r + 3) * n], Tm[r + 3 + q * n], a3);
-      }
-      for (; r <= q; ++r) a0 = fma(Tm[p + r * n], Tm[r + q * n], a0);
-      Wt[pair * bb + pl + ql * b] = (a0 + a1) + (a2 + a3);
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
-      const int g = idx / per, r0 = idx - g * per;
-      const int pair = r0 / bb, rem = r0 % bb;
-      const int ql = rem % b, pl = rem / b;
-      const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
-      if (q >= n) continue;
-      T* Tm = base + g * stride;
-      const T* Wt = base + g * stride + (size_t)n * n;
-      const T* w = Wt + pair * bb + ql * b - s;
-      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-      int r = p;
-      for (; r + 3 < s + b; r += 4) {
-        a0 = fma(Tm[p + r * n], w[r], a0);
-        a1 = fma(Tm[p + (r + 1) * n], w[r + 1], a1);
-        a2 = fma(Tm[p + (r + 2) * n], w[r + 2], a2);
-        a3 = fma(Tm[p + (r + 3) * n], w[r + 3], a3);
-      }
-      for (; r < s + b; ++r) a0 = fma(Tm[p + r * n], w[r], a0);
-      Tm[p + q * n] = -((a0 + a1) + (a2 + a3));
-    }
-    __syncthreads();
-  }
 }
 
 // Factors nodes node0 .. node0+G-1 of a tree level of arity Q: children
@@ -396,7 +343,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
     for (int gq = warp; gq < cnt * n; gq += NT / 32) {
       const int gl = gq / n, q = gq - gl * n, g = g0 + gl;
       const int64_t node = node0 + g;
-      T* Tm = D + gl * tstride + (size_t)q * n;
+      T* Tm = D + gl * tstride + (size_t)q * t_ld(n);
       for (int p = lane; p < n; p += 32) {
         T v = T(0);
         if (p == q) v = (T)tau_s[g * n + p];
@@ -405,12 +352,12 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
       }
     }
     __syncthreads();
-    build_t_doubling_batch(D, tstride, cnt, n);
+    build_t_doubling_many(D, tstride, D + (size_t)n * t_ld(n), tstride, cnt, n);
     for (int gq = warp; gq < cnt * n; gq += NT / 32) {
       const int gl = gq / n, q = gq - gl * n;
       const int64_t node = node0 + g0 + gl;
       if (node < nodes)
-        for (int p = lane; p < n; p += 32) Tout[node * nn + (int64_t)q * n + p] = D[gl * tstride + (size_t)q * n + p];
+        for (int p = lane; p < n; p += 32) Tout[node * nn + (int64_t)q * n + p] = D[gl * tstride + (size_t)q * t_ld(n) + p];
     }
     __syncthreads();
   }

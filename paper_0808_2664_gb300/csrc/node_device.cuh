@@ -13,7 +13,7 @@ constexpr int kMinRowsNode = 4;
 
 __host__ __device__ inline size_t align_up_n(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline int node_ld(int n) { return n | 1; }
+__host__ __device__ inline int node_ld(int n) { return (n + 1) | 1; }  // odd, and room for T's t_ld(n)
 
 __host__ __device__ inline size_t node_tile_bytes(int n, int q, size_t elem) {
   const size_t tile = align_up_n(elem * (size_t)q * n * node_ld(n), 16);
@@ -178,11 +178,12 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
   if (kBuildT) {
     // T lives in block 0's region (R already written out); the doubling
     // workspace reuses block 1's region once Z no longer needs Y.
-    T* Tm = S;
+    T* Tm = S;  // leading dimension t_ld(n) <= ld
     T* Wt = S + (size_t)n * ld;
+    const int L = t_ld(n);
     for (int64_t idx = tid; idx < nn; idx += NT) {  // diagonal and below; Z fills above
       const int p = (int)(idx % n), jj = (int)(idx / n);
-      if (p >= jj) Tm[idx] = p == jj ? (T)tau_s[p] : T(0);
+      if (p >= jj) Tm[p + (int64_t)jj * L] = p == jj ? (T)tau_s[p] : T(0);
     }
     // Pairs (p, j), p < j, p-major: the lanes of a warp share p, so every
     // lane runs the same (nc - 1)(p + 1)-term sum.
@@ -197,11 +198,11 @@ __device__ void node_factor_one(const T* Rin, int nc, int q, int n, T* Ro, T* Yo
       T z = T(0);
       for (int b = 1; b < nc; ++b)
         for (int i = 0; i <= p; ++i) z = fma(at(b, p, i), at(b, jj, i), z);
-      Tm[p + (int64_t)jj * n] = z;
+      Tm[p + (int64_t)jj * L] = z;
     }
     __syncthreads();
     build_t_doubling(Tm, Wt, n);
-    for (int64_t idx = tid; idx < nn; idx += NT) To[idx] = Tm[idx];
+    for (int64_t idx = tid; idx < nn; idx += NT) To[idx] = Tm[idx % n + (idx / n) * L];
     __syncthreads();
   }
 }

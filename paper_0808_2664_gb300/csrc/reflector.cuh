@@ -123,43 +123,86 @@ __device__ __forceinline__ double scaled_norm(int len, Get get) {
 
 __device__ __forceinline__ int pow2_floor(int x) { return x <= 1 ? 1 : 1 << (31 - __clz(x)); }
 
-// Build the compact-WY T (upper triangular, n x n, column-major ld n, shared
-// memory, in the product type T) in place.  On entry Tm holds tau on the diagonal, the
-// strictly upper part of Y^T Y above it (Tm(p, q) = y_p^T y_q) and zeros
-// below.  Schreiber and Van Loan (cited in Section 2.1) give, for two blocks
-// of reflectors, I - Y T Y^T with T = [T1, -T1 (Y1^T Y2) T2; 0, T2]; applying
-// that merge to aligned blocks of 1, 2, 4, ... columns builds T in log2(n)
-// levels of independent triangular products.  Wt needs n*n/2 doubles.  Every
-// thread of the block calls this.
+// Layout of T while it is built: column-major with leading dimension n + 1,
+// so that the lanes of a warp walking along a row of T hit different shared
+// memory banks; the doubling workspace pads its b x b blocks likewise.
+__host__ __device__ inline int t_ld(int n) { return n + 1; }
+__host__ __device__ inline size_t t_work_elems(int n) {
+  size_t m = 1;
+  for (int b = 1; b < n; b *= 2) {
+    const size_t v = (size_t)((n + 2 * b - 1) / (2 * b)) * b * (b + 1);
+    if (v > m) m = v;
+  }
+  return m;
+}
+
+// Build the compact-WY T (upper triangular, n x n, shared memory, in the
+// product type T) of `count` reflector sets at once, in place: set g has
+// its T at Tm0 + g * tm_stride (leading dimension t_ld(n)) and workspace at
+// Wt0 + g * wt_stride (t_work_elems(n) entries).  On entry T holds tau on the
+// diagonal, the strictly upper part of Y^T Y above it (T(p, q) = y_p^T y_q)
+// and zeros below.  Schreiber and Van Loan (cited in Section 2.1) give, for
+// two blocks of reflectors, I - Y T Y^T with T = [T1, -T1 (Y1^T Y2) T2; 0,
+// T2]; applying that merge to aligned blocks of 1, 2, 4, ... columns builds
+// T in log2(n) levels of independent triangular products.  Every thread of
+// the block calls this.
 template <typename T>
-__device__ __forceinline__ void build_t_doubling(T* Tm, T* Wt, int n) {
+__device__ __forceinline__ void build_t_doubling_many(T* Tm0, size_t tm_stride, T* Wt0, size_t wt_stride, int count,
+                                                      int n) {
+  const int L = t_ld(n);
   for (int b = 1; b < n; b *= 2) {
     const int npairs = (n + 2 * b - 1) / (2 * b);
-    const int bb = b * b;
-    // Pass 1: W = Z12 T2 for every pair, W(p - s, q - s - b) stored at Wt + pair * b * b.
-    for (int idx = threadIdx.x; idx < npairs * bb; idx += blockDim.x) {
-      const int pair = idx / bb, rem = idx % bb;
+    const int bb = b * b, bs = b * (b + 1);
+    const int per = npairs * bb;
+    // Pass 1: W = Z12 T2 for every pair, W(p - s, q - s - b) at pl + ql (b + 1).
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+      const int g = idx / per, r0 = idx - g * per;
+      const int pair = r0 / bb, rem = r0 - pair * bb;
       const int pl = rem % b, ql = rem / b;
       const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
       if (q >= n) continue;
-      T acc = T(0);
-      for (int r = s + b; r <= q; ++r) acc = fma(Tm[p + r * n], Tm[r + q * n], acc);
-      Wt[pair * bb + pl + ql * b] = acc;
+      const T* Tm = Tm0 + g * tm_stride;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int r = s + b;
+      for (; r + 3 <= q; r += 4) {
+        a0 = fma(Tm[p + r * L], Tm[r + q * L], a0);
+        a1 = fma(Tm[p + (r + 1) * L], Tm[r + 1 + q * L], a1);
+        a2 = fma(Tm[p + (r + 2) * L], Tm[r + 2 + q * L], a2);
+        a3 = fma(Tm[p + (r + 3) * L], Tm[r + 3 + q * L], a3);
+      }
+      for (; r <= q; ++r) a0 = fma(Tm[p + r * L], Tm[r + q * L], a0);
+      Wt0[g * wt_stride + pair * bs + pl + ql * (b + 1)] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     // Pass 2: T12 = -T1 W; the lanes of a warp share p, so their sums have
     // the same length.
-    for (int idx = threadIdx.x; idx < npairs * bb; idx += blockDim.x) {
-      const int pair = idx / bb, rem = idx % bb;
+    for (int idx = threadIdx.x; idx < count * per; idx += blockDim.x) {
+      const int g = idx / per, r0 = idx - g * per;
+      const int pair = r0 / bb, rem = r0 - pair * bb;
       const int ql = rem % b, pl = rem / b;
       const int s = pair * 2 * b, p = s + pl, q = s + b + ql;
       if (q >= n) continue;
-      T acc = T(0);
-      for (int r = p; r < s + b; ++r) acc = fma(Tm[p + r * n], Wt[pair * bb + (r - s) + ql * b], acc);
-      Tm[p + q * n] = -acc;
+      T* Tm = Tm0 + g * tm_stride;
+      const T* w = Wt0 + g * wt_stride + pair * bs + ql * (b + 1) - s;
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int r = p;
+      for (; r + 3 < s + b; r += 4) {
+        a0 = fma(Tm[p + r * L], w[r], a0);
+        a1 = fma(Tm[p + (r + 1) * L], w[r + 1], a1);
+        a2 = fma(Tm[p + (r + 2) * L], w[r + 2], a2);
+        a3 = fma(Tm[p + (r + 3) * L], w[r + 3], a3);
+      }
+      for (; r < s + b; ++r) a0 = fma(Tm[p + r * L], w[r], a0);
+      Tm[p + q * L] = -((a0 + a1) + (a2 + a3));
     }
     __syncthreads();
   }
+}
+
+// One reflector set: T at Tm (leading dimension t_ld(n)), workspace at Wt.
+template <typename T>
+__device__ __forceinline__ void build_t_doubling(T* Tm, T* Wt, int n) {
+  build_t_doubling_many(Tm, 0, Wt, 0, 1, n);
 }
 
 }  // namespace tsqr
