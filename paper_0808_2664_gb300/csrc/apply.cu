@@ -20,6 +20,12 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16;
 // ---------------------------------------------------------------- leaves --
 // Shared memory: Ys [kApplyRows][n+1] (row-major), Cs [kApplyRows][kc+1],
 // Ws [n][kc] (W, then T-times-W), Ts [n][n] (column-major T).
+// Whether a leaf's n x n T fits in the Y and C staging tiles (it is needed
+// only after they are done with).
+__host__ __device__ inline bool leaf_apply_t_shared(int n, size_t elem) {
+  return elem * (size_t)n * n <= align16(elem * kApplyRows * (n + 1)) + align16(elem * kApplyRows * (kApplyCols + 1));
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -30,7 +36,9 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   T* Ys = reinterpret_cast<T*>(smem);
   T* Cs = reinterpret_cast<T*>(smem + align16(sizeof(T) * RB * ly));
   T* Ws = reinterpret_cast<T*>(smem + align16(sizeof(T) * RB * ly) + align16(sizeof(T) * RB * lc));
-  T* Ts = Ws + (size_t)n * KC;
+  // T is needed only between phases 1 and 3: it reuses the staging area when it fits.
+  const bool t_shared = leaf_apply_t_shared(n, sizeof(T));
+  T* Ts = t_shared ? Ys : Ws + (size_t)n * KC;
   const int tid = threadIdx.x;
 
   const int64_t leaf = blockIdx.x;
@@ -45,7 +53,8 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
 
   // T of this leaf (column-major n x n).
   const T* Tg = a.Tw + leaf * (int64_t)n * n;
-  for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
+  if (!t_shared)
+    for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
 
   // Phase 1: W = Y^T C over rows1 rows; 4x4 register tiles of W.
   const int tp = (n + 3) / 4, tcn = (kc + 3) / 4;
@@ -58,21 +67,74 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
 #pragma unroll
       for (int y = 0; y < 4; ++y) acc[t][x][y] = T(0);
 
-  for (int rb = 0; rb < rows1; rb += RB) {
-    __syncthreads();
-    for (int idx = tid; idx < RB * n; idx += NT) {
-      const int i = idx % RB, p = idx / RB;
-      const int r = rb + i;
+  // Staging of the next 32-row block of Y and C goes through registers:
+  // its global loads are issued before the current block's products.
+  constexpr bool kPrefetch = sizeof(T) == 4;  // for FP64 the registers cost more occupancy than the overlap gains
+  constexpr int kYPer = kPrefetch ? (RB * kMaxN + NT - 1) / NT : 1, kCPer = kPrefetch ? (RB * KC + NT - 1) / NT : 1;
+  T ypre[kYPer], cpre[kCPer];
+  auto fetch_y = [&](int rb, int rows) {
+#pragma unroll
+    for (int j = 0; j < kYPer; ++j) {
+      const int idx = tid + j * NT;
       T v = T(0);
-      if (r < rows1) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
+      if (idx < RB * n) {
+        const int i = idx % RB, p = idx / RB, r = rb + i;
+        if (r < rows) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
+      }
+      ypre[j] = v;
+    }
+  };
+  auto direct_y = [&](int rb, int rows) {
+    for (int idx = tid; idx < RB * n; idx += NT) {
+      const int i = idx % RB, p = idx / RB, r = rb + i;
+      T v = T(0);
+      if (r < rows) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
       Ys[i * ly + p] = v;
     }
-    for (int idx = tid; idx < RB * KC; idx += NT) {
-      const int i = idx % RB, c = idx / RB;
-      const int r = rb + i;
-      Cs[i * lc + c] = (r < rows1 && c < kc) ? Cg[r + (int64_t)c * a.ldc] : T(0);
+  };
+  auto stage_y = [&]() {
+#pragma unroll
+    for (int j = 0; j < kYPer; ++j) {
+      const int idx = tid + j * NT;
+      if (idx < RB * n) Ys[(idx % RB) * ly + idx / RB] = ypre[j];
+    }
+  };
+  auto fetch_c = [&](int rb) {
+#pragma unroll
+    for (int j = 0; j < kCPer; ++j) {
+      const int idx = tid + j * NT;
+      const int i = idx % RB, c = idx / RB, r = rb + i;
+      cpre[j] = (idx < RB * KC && r < rows1 && c < kc) ? Cg[r + (int64_t)c * a.ldc] : T(0);
+    }
+  };
+  auto stage_c = [&]() {
+#pragma unroll
+    for (int j = 0; j < kCPer; ++j) {
+      const int idx = tid + j * NT;
+      if (idx < RB * KC) Cs[(idx % RB) * lc + idx / RB] = cpre[j];
+    }
+  };
+  if (kPrefetch) {
+    fetch_y(0, rows1);
+    fetch_c(0);
+  }
+  for (int rb = 0; rb < rows1; rb += RB) {
+    __syncthreads();
+    if (kPrefetch) {
+      stage_y();
+      stage_c();
+    } else {
+      direct_y(rb, rows1);
+      for (int idx = tid; idx < RB * KC; idx += NT) {
+        const int i = idx % RB, c = idx / RB, r = rb + i;
+        Cs[i * lc + c] = (r < rows1 && c < kc) ? Cg[r + (int64_t)c * a.ldc] : T(0);
+      }
     }
     __syncthreads();
+    if (kPrefetch && rb + RB < rows1) {
+      fetch_y(rb + RB, rows1);
+      fetch_c(rb + RB);
+    }
     const int rmax = min(RB, rows1 - rb);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -104,6 +166,8 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
       for (int y = 0; y < 4; ++y)
         if (p0 + x < n && c0 + y < KC) Ws[(p0 + x) * KC + c0 + y] = acc[t][x][y];
   }
+  if (t_shared)
+    for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
   __syncthreads();
 
   // Phase 2: W <- T^T W (Q^T) or T W (Q, form).
@@ -144,16 +208,13 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   // Phase 3: C <- C - Y W  (form: C <- [X; 0] - Y W).  Thread = (row, column group).
   constexpr int CG = NT / RB;
   const int i = tid % RB, cg = tid / RB;
+  if (kPrefetch) fetch_y(0, hl);
   for (int rb = 0; rb < hl; rb += RB) {
     __syncthreads();
-    for (int idx = tid; idx < RB * n; idx += NT) {
-      const int ii = idx % RB, p = idx / RB;
-      const int r = rb + ii;
-      T v = T(0);
-      if (r < hl) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
-      Ys[ii * ly + p] = v;
-    }
+    if (kPrefetch) stage_y();
+    else direct_y(rb, hl);
     __syncthreads();
+    if (kPrefetch && rb + RB < hl) fetch_y(rb + RB, hl);
     const int r = rb + i;
     if (r < hl) {
       const int pmax = min(n, r + 1);  // Y(r, p) = 0 for p > r
@@ -326,7 +387,7 @@ inline unsigned small_grid(int64_t work) {
 
 size_t leaf_apply_smem(int n, size_t elem) {
   return align16(elem * kApplyRows * (n + 1)) + align16(elem * kApplyRows * (kApplyCols + 1)) +
-         elem * (size_t)n * kApplyCols + elem * (size_t)n * n;
+         elem * (size_t)n * kApplyCols + (leaf_apply_t_shared(n, elem) ? 0 : elem * (size_t)n * n);
 }
 
 size_t node_apply_smem(int n, int q, size_t elem) {
