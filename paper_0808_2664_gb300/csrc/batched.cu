@@ -50,7 +50,6 @@ struct BMat {
   int32_t levels;
   int32_t ld_s;
   T* leafR;
-  T* leafT;
   T* leafTau;
   T* d;
   int32_t lvl0;  // index of this matrix's level 1 in the level table
@@ -257,8 +256,6 @@ int build_batch(tsqr_batch_s* b, const int64_t* m, const int64_t* n, void* const
     const size_t nnb = (size_t)ni * ni * es, nvb = (size_t)ni * es;
     M.leafR = (T*)off;
     off += al256(nl * nnb);
-    M.leafT = (T*)off;
-    off += al256(nl * nnb);
     M.leafTau = (T*)off;
     off += al256(nl * nvb);
     M.d = (T*)off;
@@ -329,7 +326,6 @@ int build_batch(tsqr_batch_s* b, const int64_t* m, const int64_t* n, void* const
   auto rebase = [&](T* p) { return (T*)(B + (size_t)p); };
   for (auto& M : mats) {
     M.leafR = rebase(M.leafR);
-    M.leafT = rebase(M.leafT);
     M.leafTau = rebase(M.leafTau);
     M.d = rebase(M.d);
   }
