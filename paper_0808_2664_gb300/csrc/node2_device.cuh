@@ -87,6 +87,21 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
   // Column c of block b (0: R_0, b: R_b) of node g, rows 0..c.
   auto col = [&](int g, int b, int c) -> T* { return D + (size_t)(Q * g + b) * pk + c * (c + 1) / 2; };
 
+  // A lone child (the last node of a level whose count leaves one over)
+  // passes up unchanged: its Q factor is the identity.  (Factoring it with
+  // zero lower blocks would give the same R but take the scaled-norm path
+  // of a zero tail at every column.)
+  if (G == 1 && node0 < nodes && (int64_t)Q * node0 + 1 >= nin) {
+    const T* src = Rin + (int64_t)Q * node0 * nn;
+    for (int64_t idx = tid; idx < nn; idx += NT) {
+      Rout[node0 * nn + idx] = __ldcg(src + idx);
+      if (kBuildT) Tout[node0 * nn + idx] = T(0);
+    }
+    for (int64_t idx = tid; idx < (int64_t)(Q - 1) * nn; idx += NT) Yout[node0 * (Q - 1) * nn + idx] = T(0);
+    for (int c = tid; c < n; c += NT) tauout[node0 * n + c] = T(0);
+    return;
+  }
+
   // Load the children's upper triangles, one warp per (node, column): the
   // triangles' column c (rows 0..c), its largest magnitude, its power-of-two
   // factor applied on the way into shared memory.
