@@ -209,7 +209,13 @@ int caqr_factor_f32(int64_t m, int64_t n, float* A, int64_t lda, int64_t b, int3
  * Plan-once form of CAQR: caqr_q_create plans every panel of an m x n
  * problem with panel width b and allocates all panel workspaces at once;
  * caqr_refactor then factors a matrix of that shape (device, lda >= m; double
- * for TSQR_PREC_FP64, float otherwise) in place with no allocation.  caqr_factor = create + refactor.
+ * for TSQR_PREC_FP64, float otherwise) in place with no allocation of
+ * device workspace.  caqr_factor = create + one factorisation.
+ * Unless stage timing is on (caqr_q_set_timing), caqr_refactor captures its
+ * panel loop into a CUDA graph on the first call for a given (A, lda) and
+ * replays that graph on the caller's stream in later calls with the same
+ * pair (a new pair is captured anew); the contents of A may change freely
+ * between calls.  Errors of the capture are returned like launch errors.
  */
 int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, const tsqr_opts_t* opts,
                   caqr_q_t* q, tsqr_stream_t stream);

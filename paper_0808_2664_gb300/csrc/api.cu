@@ -93,6 +93,13 @@ struct caqr_q_s {
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> ev_left, ev_fact;
   int32_t upd = TSQR_PREC_FP64;  // trailing-update arithmetic
+  // caqr_refactor's panel loop as a CUDA graph, captured for one (A, lda)
+  // on a private stream and replayed on the caller's stream.
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  void* graph_A = nullptr;
+  int64_t graph_lda = 0;
+  bool timing = false;
 };
 
 namespace {
@@ -811,13 +818,8 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
   return TSQR_OK;
 }
 
-int caqr_refactor(caqr_q_t c, void* A, int64_t lda, tsqr_stream_t stream) {
-  if (!valid(c)) return TSQR_ERR_HANDLE;
-  if (!A) return -2;
-  if (lda < c->m) return -3;
-  cudaStream_t s = (cudaStream_t)stream;
-  c->A = A;
-  c->lda = lda;
+// Issues the panel loop on s (the caller's stream, or the capture stream).
+static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
   // Right-looking loop with a look-ahead of one panel (Section 3's panel
   // loop; the overlap is this implementation's): panel j+1's columns get
   // (Q_j D_j)^T first, then panel j+1 is factored on the side stream while
@@ -852,13 +854,53 @@ int caqr_refactor(caqr_q_t c, void* A, int64_t lda, tsqr_stream_t stream) {
   return TSQR_OK;
 }
 
+int caqr_refactor(caqr_q_t c, void* A, int64_t lda, tsqr_stream_t stream) {
+  if (!valid(c)) return TSQR_ERR_HANDLE;
+  if (!A) return -2;
+  if (lda < c->m) return -3;
+  cudaStream_t s = (cudaStream_t)stream;
+  c->A = A;
+  c->lda = lda;
+  // With stage timing on, the loop runs directly (its events time real
+  // launches).  Otherwise the loop (a few thousand launches at n = 8192,
+  // whose host-side cost would otherwise pace the late, small panels) is
+  // captured once per (A, lda) and replayed as one graph launch.
+  if (c->timing) return caqr_issue(c, A, lda, s);
+  if (!c->graph || c->graph_A != A || c->graph_lda != lda) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return TSQR_ERR_CUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return TSQR_ERR_CUDA;
+    const int rc = caqr_issue(c, A, lda, c->cap);
+    const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (rc != TSQR_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_err(e);
+    const cudaError_t ei = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      c->graph = nullptr;
+      return cuda_err(ei);
+    }
+    c->graph_A = A;
+    c->graph_lda = lda;
+  }
+  return cuda_err(cudaGraphLaunch(c->graph, s));
+}
+
 static int caqr_factor_any(int64_t m, int64_t n, void* A, int64_t lda, int64_t b, int32_t update_precision,
                            const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream) {
   cudaStream_t s = (cudaStream_t)stream;
   caqr_q_t c = nullptr;
   int rc = caqr_q_create(m, n, b, update_precision, opts, &c, stream);
   if (rc != TSQR_OK) return rc == -5 ? -7 : rc;
-  rc = caqr_refactor(c, A, lda, stream);
+  // One factorisation: the loop runs directly (a graph would not be reused).
+  c->A = A;
+  c->lda = lda;
+  rc = caqr_issue(c, A, lda, s);
   if (rc != TSQR_OK || !q) {
     cudaStreamSynchronize(s);
     caqr_q_destroy(c);
@@ -945,6 +987,7 @@ int caqr_form_q(caqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream) {
 
 int caqr_q_set_timing(caqr_q_t q, int32_t enable) {
   if (!valid(q)) return TSQR_ERR_HANDLE;
+  q->timing = enable != 0;
   for (auto* p : q->panels) tsqr_q_set_timing(p, enable);
   return TSQR_OK;
 }
@@ -994,6 +1037,8 @@ int caqr_q_destroy(caqr_q_t q) {
     if (e) cudaEventDestroy(e);
   for (auto* p : q->panels) destroy_handle(p);
   cudaError_t e = q->ws ? cudaFree(q->ws) : cudaSuccess;
+  if (q->graph) cudaGraphExecDestroy(q->graph);
+  if (q->cap) cudaStreamDestroy(q->cap);
   delete q;
   return cuda_err(e);
 }

@@ -56,7 +56,10 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   if (!t_shared)
     for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
 
-  // Phase 1: W = Y^T C over rows1 rows; 4x4 register tiles of W.
+  // Phase 1: W = Y^T C over rows1 rows; 4x4 register tiles of W.  Tiles
+  // are numbered column-tile fastest, so that the lanes of a warp share one
+  // or two row tiles p0 and the triangular bounds below (Y(r, p) = 0 for
+  // r < p; T triangular) are nearly uniform over the warp and skip the zeros.
   const int tp = (n + 3) / 4, tcn = (kc + 3) / 4;
   const int ntiles = tp * tcn;
   T acc[2][4][4];
@@ -140,8 +143,8 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
     for (int t = 0; t < 2; ++t) {
       const int tile = tid + t * NT;
       if (tile >= ntiles) break;
-      const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
-      for (int i = 0; i < rmax; ++i) {
+      const int p0 = (tile / tcn) * 4, c0 = (tile % tcn) * 4;
+      for (int i = p0 > rb ? p0 - rb : 0; i < rmax; ++i) {  // rows above p0: zero in Y
         T yv[4], cv[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) yv[x] = (p0 + x < n) ? Ys[i * ly + p0 + x] : T(0);
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   for (int t = 0; t < 2; ++t) {
     const int tile = tid + t * NT;
     if (tile >= ntiles) break;
-    const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
+    const int p0 = (tile / tcn) * 4, c0 = (tile % tcn) * 4;
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   for (int t = 0; t < 2; ++t) {
     const int tile = tid + t * NT;
     if (tile >= ntiles) break;
-    const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
+    const int p0 = (tile / tcn) * 4, c0 = (tile % tcn) * 4;
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
       const int p = p0 + x;
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   for (int t = 0; t < 2; ++t) {
     const int tile = tid + t * NT;
     if (tile >= ntiles) break;
-    const int p0 = (tile % tp) * 4, c0 = (tile / tp) * 4;
+    const int p0 = (tile / tcn) * 4, c0 = (tile % tcn) * 4;
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -232,7 +235,9 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
 // ----------------------------------------------------------------- nodes --
 // Shared memory (column-major tiles, ldn odd): B1 [kc][ldn] holds a lower
 // slot while W accumulates and then W' = T^(T) W; B2 [kc][ldn] holds W and
-// later Y_b W'; Ys [n][ldn] one lower block of Y; Ts [n][n].
+// later Y_b W'; Ys [n][ldn] one lower block of Y, and T ([n][n]) between
+// the W accumulation and the Y_b W' products (two CTAs per SM at n = 64 in
+// FP64).
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
   T* B1 = reinterpret_cast<T*>(smem);
   T* B2 = B1 + (size_t)KC * ldn;
   T* Ys = B2 + (size_t)KC * ldn;
-  T* Ts = Ys + (size_t)n * ldn;
+  T* Ts = Ys;
   const int tid = threadIdx.x;
   const int64_t node = blockIdx.x;
   const int64_t c0 = node * q;
@@ -264,7 +269,6 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
     }
   };
 
-  for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
   {  // W = C_0 (form: X)
     const T* src = slot_ptr(0);
     for (int idx = tid; idx < n * kc; idx += NT) {
@@ -294,6 +298,8 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
       }
     }
   }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
   __syncthreads();
   // W' = T^T W (Q^T) or T W (Q, form), into B1.
   if (cc < kc) {
@@ -393,7 +399,7 @@ size_t leaf_apply_smem(int n, size_t elem) {
 size_t node_apply_smem(int n, int q, size_t elem) {
   (void)q;
   const int ldn = n | 1;
-  return elem * ((size_t)2 * kApplyCols * ldn + (size_t)n * ldn + (size_t)n * n);
+  return elem * ((size_t)2 * kApplyCols * ldn + (size_t)n * ldn);
 }
 
 template <typename T>

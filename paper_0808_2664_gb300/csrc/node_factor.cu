@@ -14,6 +14,8 @@
 // 0 followed by rows 0..j of blocks 1..q-1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "node2_device.cuh"
 #include "node_device.cuh"
 #include "tsqr_internal.cuh"
@@ -69,15 +71,15 @@ size_t node2_factor_smem_min(int n, int q, size_t elem) { return node2_smem_byte
 template <typename T>
 cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
   if (a.nodes <= 0 || a.n <= 0) return cudaSuccess;
+  int dev = 0, sms = 0, smax = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (a.arity == 2 || a.arity == 4) {
     // Binary wide levels: two nodes per CTA share each serial step (when
     // their tiles fit); narrow binary levels (fewer groups than about two per
     // SM) and arity 4: one node per CTA, three CTAs per SM at n = 64 (measured
     // faster for the four-triangle nodes, whose steps are three times wider).
-    int dev = 0, sms = 0, smax = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (a.arity == 2) {
       const bool wide = a.nodes >= 4 * (int64_t)sms;
       if (wide && node2_smem_bytes(a.n, 2, sizeof(T), 256, 2) <= (size_t)smax) return launch_node2<T, 256, 2, 2>(a, sms, s);
@@ -85,13 +87,15 @@ cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
     }
     return launch_node2<T, 256, 1, 4>(a, sms, s);
   }
+  // Arity 8 and 16 (short trees over few leaves, e.g. CAQR panels): the
+  // packed lock-step kernel when its triangles fit, else the dense one.
+  if ((a.arity == 8 || a.arity == 16) && node2_smem_bytes(a.n, 1, sizeof(T), 256, a.arity) <= (size_t)smax)
+    return a.arity == 8 ? launch_node2<T, 256, 1, 8>(a, sms, s) : launch_node2<T, 256, 1, 16>(a, sms, s);
   const size_t smem = node_smem_bytes(a.n, a.arity, sizeof(T), kNodeThreads);
   auto kern = node_factor_kernel<T, kNodeThreads>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNodeThreads, smem);
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)sms * per_sm;
@@ -102,7 +106,9 @@ cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
 
 size_t node_factor_smem(int n, int q, size_t elem) {
   if (q == 2 || q == 4) return node2_factor_smem_min(n, q, elem);
-  return node_smem_bytes(n, q, elem, kNodeThreads);
+  const size_t dense = node_smem_bytes(n, q, elem, kNodeThreads);
+  if (q == 8 || q == 16) return std::min(node2_factor_smem_min(n, q, elem), dense);
+  return dense;
 }
 
 template cudaError_t launch_node_factor<double>(const NodeFactorArgs<double>&, cudaStream_t);

@@ -44,6 +44,8 @@ SHAPES = [
     (5000, 16, 128, 4),   # arity-4 tree with a short last node
     (2049, 1, 256, 2),    # one column
     (777, 3, 32, 3),      # arity 3
+    (20000, 64, 256, 8),  # arity 8: 79 leaves, a top node with two children
+    (9000, 32, 128, 16),  # arity 16: 70 leaves, a short last node
     (20000, 64, 256, 2),  # several tree levels, odd leaf counts
     (3000, 128, 128, 2),  # the widest n
 ]
