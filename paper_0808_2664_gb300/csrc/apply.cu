@@ -41,9 +41,21 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   T* Ts = t_shared ? Ys : Ws + (size_t)n * KC;
   const int tid = threadIdx.x;
 
-  const int64_t leaf = blockIdx.x;
-  const int64_t k0 = (int64_t)blockIdx.y * KC;
-  const int kc = (int)((a.k - k0) < KC ? (a.k - k0) : KC);
+  int64_t unit = blockIdx.x;
+  int piece = 0, pieces = 1;
+  if (unit >= a.split_from) {
+    const int64_t v = unit - a.split_from;
+    unit = a.split_from + v / a.split;
+    piece = (int)(v % a.split);
+    pieces = a.split;
+  }
+  const int64_t leaf = unit % a.nleaves;
+  const int64_t kchunk = (unit / a.nleaves) * KC;
+  const int kfull = (int)((a.k - kchunk) < KC ? (a.k - kchunk) : KC);
+  const int pw = (kfull + pieces - 1) / pieces;
+  const int64_t k0 = kchunk + (int64_t)piece * pw;
+  const int kc = kfull - piece * pw < pw ? kfull - piece * pw : pw;
+  if (kc <= 0) return;  // an empty piece of a narrow chunk (uniform over the CTA)
   const int64_t r0 = leaf * a.h;
   const int hl = (leaf == a.nleaves - 1) ? (int)(a.m - r0) : (int)a.h;
   const T* Yg = a.Y + r0;
@@ -249,12 +261,24 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
   T* Ys = B2 + (size_t)KC * ldn;
   T* Ts = Ys;
   const int tid = threadIdx.x;
-  const int64_t node = blockIdx.x;
+  int64_t unit = blockIdx.x;
+  int piece = 0, pieces = 1;
+  if (unit >= a.split_from) {
+    const int64_t v = unit - a.split_from;
+    unit = a.split_from + v / a.split;
+    piece = (int)(v % a.split);
+    pieces = a.split;
+  }
+  const int64_t node = unit % a.nodes;
   const int64_t c0 = node * q;
   const int nc = (int)((a.nin - c0) < q ? (a.nin - c0) : q);
   if (nc <= 1) return;  // a lone child: identity
-  const int64_t k0 = (int64_t)blockIdx.y * KC;
-  const int kc = (int)((a.k - k0) < KC ? (a.k - k0) : KC);
+  const int64_t kchunk = (unit / a.nodes) * KC;
+  const int kfull = (int)((a.k - kchunk) < KC ? (a.k - kchunk) : KC);
+  const int kw = KC / pieces;  // columns of this CTA's piece (a power of two)
+  const int64_t k0 = kchunk + (int64_t)piece * kw;
+  const int kc = kfull - piece * kw < kw ? kfull - piece * kw : kw;
+  if (kc <= 0) return;
   const int64_t nn = (int64_t)n * n;
   const T* Yn = a.Y + node * (int64_t)(q - 1) * nn;
   const T* Tg = a.Tw + node * nn;
@@ -276,8 +300,8 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
       B2[c * ldn + i] = src[i + (int64_t)c * a.ldc];
     }
   }
-  constexpr int PG = NT / KC;
-  const int cc = tid % KC, pg = tid / KC;
+  const int PG = NT / kw;  // threads per column: one column per lane, PG rows apart
+  const int cc = tid % kw, pg = tid / kw;
   if (mode != kApplyForm) {
     // W += Y_b^T C_b; Y_b is upper triangular, so W(p) sums rows i <= p.
     for (int b = 1; b < nc; ++b) {
@@ -402,6 +426,32 @@ size_t node_apply_smem(int n, int q, size_t elem) {
   return elem * ((size_t)2 * kApplyCols * ldn + (size_t)n * ldn);
 }
 
+// Tail split of a grid of equal work units, one per CTA: with S resident
+// CTAs, units = w S + f, and the last f units run as a partial wave.  Cut
+// into p column pieces they take ceil(p f / S) / p of a wave instead of one
+// (each piece costs a little more than its share: Y and T are staged again).
+// Returns p (1: no split) and the first unit that is split.
+template <typename K>
+int tail_split(K kern, size_t smem, int64_t units, int pmax, int64_t* split_from) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kApplyThreads, smem);
+  const int64_t S = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  const int64_t f = units % S;
+  int split = 1;
+  double best = 1.0;
+  for (int p = 2; f > 0 && p <= pmax; p *= 2) {
+    const double t = (double)((p * f + S - 1) / S) / p + 0.04 * (p - 1);
+    if (t < best) {
+      best = t;
+      split = p;
+    }
+  }
+  *split_from = split > 1 ? units - f : units;
+  return split;
+}
+
 template <typename T>
 cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s) {
   if (a.nleaves <= 0 || a.k <= 0 || a.n <= 0) return cudaSuccess;
@@ -410,9 +460,14 @@ cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t kchunks = (a.k + kApplyCols - 1) / kApplyCols;
-  if (kchunks > 65535 || a.nleaves > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)a.nleaves, (unsigned)kchunks);
-  kern<<<grid, kApplyThreads, smem, s>>>(a);
+  const int64_t units = a.nleaves * kchunks;
+  // Quarter pieces (16 columns) only in form mode: in the apply modes
+  // W = Y^T C runs over all h rows, and 16 columns give it two warps per CTA.
+  LeafApplyArgs<T> b = a;
+  b.split = tail_split(kern, smem, units, a.mode == kApplyForm ? 4 : 2, &b.split_from);
+  const int64_t grid = b.split_from + (units - b.split_from) * b.split;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  kern<<<(unsigned)grid, kApplyThreads, smem, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -424,9 +479,11 @@ cudaError_t launch_node_apply(const NodeApplyArgs<T>& a, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t kchunks = (a.k + kApplyCols - 1) / kApplyCols;
-  if (kchunks > 65535 || a.nodes > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  dim3 grid((unsigned)a.nodes, (unsigned)kchunks);
-  kern<<<grid, kApplyThreads, smem, s>>>(a);
+  NodeApplyArgs<T> b = a;
+  b.split = tail_split(kern, smem, a.nodes * kchunks, 4, &b.split_from);
+  const int64_t grid = b.split_from + (a.nodes * kchunks - b.split_from) * b.split;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  kern<<<(unsigned)grid, kApplyThreads, smem, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -77,6 +77,11 @@ struct LeafApplyArgs {
   int64_t ldc;
   int64_t k;
   int mode;         // ApplyMode
+  // Set by the launcher: work units (leaf, 64-column chunk), leaf fastest,
+  // one per CTA; units from split_from on are cut into `split` column
+  // pieces (CTAs), so that the last, partial wave is made of short pieces.
+  int64_t split_from;
+  int split;
 };
 
 template <typename T>
@@ -92,6 +97,10 @@ struct NodeApplyArgs {
   int64_t ldc;
   int64_t k;
   int mode;
+  // Set by the launcher: units (node, 64-column chunk), node fastest; units
+  // from split_from on are cut into `split` column pieces.
+  int64_t split_from;
+  int split;
 };
 
 template <typename T>
