@@ -761,7 +761,8 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
     }
     // Panels take the plain TSQR default (the tallest leaf that fits): the
     // tree part of each trailing update is about n / h of its leaf part.
-    // The BF16x3 update kernel stages at most kBf16x3MaxLeaf rows per leaf.
+    // BF16x3 panels: power-of-two leaves of at most kBf16x3MaxLeaf rows
+    // (512 at b = 64 in FP32: two tree levels per 8192-row panel).
     tsqr_opts_t po = opts ? *opts : tsqr_opts_t{0, 0, 0};
     if (po.leaf_rows == 0 && update_precision == TSQR_UPDATE_BF16X3) {
       int64_t h = 1;

@@ -1,6 +1,6 @@
 // Leaf-block trailing update of CAQR on the 5th-generation tensor cores.
 //
-// For every leaf i of a panel (h_i <= 256 rows, n <= 64 reflectors) and a
+// For every leaf i of a panel (n <= 64 reflectors, any height) and a
 // 128-column slice of the trailing matrix C (FP32 storage), one CTA computes
 //     C_i <- C_i - Y_i (T_i^T (Y_i^T C_i))
 // (the leaf phase of Section 3.1's trailing update, Q_i^T in compact-WY

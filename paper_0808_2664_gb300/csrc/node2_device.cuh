@@ -17,8 +17,9 @@
 //     by warp 0 while the other warps apply H_{k-1} to every trailing column
 //     fused with that column's dot with column k's unscaled tail, and take
 //     the entries Z(p, k) = u_p^T u_k of the T factor as extra work items;
-//     then one warp per node turns the partial dots into coefficients and
-//     carries column k+1 through H_k and its squared norm; two barriers per
+//     then, per node, one warp carries column k+1 through H_k (forming its
+//     coefficient itself) and sums its squared norm while a second warp
+//     turns the other partial dots into coefficients; two barriers per
 //     column;
 //   * stores the triangles packed (column c of a block holds rows 0..c), so
 //     that a node takes n(n+1) values of shared memory.
@@ -69,7 +70,7 @@ __host__ __device__ inline size_t node2_smem_bytes(int n, int G, size_t elem, in
 template <typename T, int NT, int G, int Q, bool kBuildT = true>
 __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64_t nodes, int64_t node0, int n,
                                    T* Rout, T* Yout, T* Tout, T* tauout, int* status, unsigned char* smem) {
-  static_assert(NT / 32 >= G + 2, "need a reflector warp, one column warp per node and a Z warp");
+  static_assert(NT / 32 >= 2 * G + 2, "need a reflector warp, two S warps per node and a Z warp");
   const int pk = node2_packed(n);
   T* D = reinterpret_cast<T*>(smem);
   unsigned char* aux = smem + node2_region_bytes(n, G, sizeof(T), Q);
@@ -254,16 +255,16 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
       }
     }
     __syncthreads();
-    // S: warp 1 + g forms the coefficients of H_k for node g's trailing
-    // columns (lanes over columns), then applies H_k to column k+1 (its
-    // coefficient comes from lane 0 by shuffle) and sums the squared tail of
-    // that column for the next reflector: R_1 rows 0..k+1.  The remaining
+    // S: warp 1 + g takes column k+1 of node g: its coefficient of H_k
+    // (every lane forms it from the partial dots), H_k applied to it, and
+    // the squared norm of its tail for the next reflector (R_1.. rows
+    // 0..k+1).  Warp 1 + G + g forms the coefficients of node g's other
+    // trailing columns (lanes over columns) at the same time; the remaining
     // warps take the Z entries of column k.
-    if (warp >= 1 && warp <= G) {
-      const int g = warp - 1;
+    if (warp >= 1 && warp <= 2 * G && acols > 0) {
+      const int g = (warp - 1) % G;
       const double tk = tau_s[g * n + k], sk = sc_s[g * n + k], ts = tk * sk;
-      T cf1 = T(0), cs1 = T(0);
-      for (int j = lane; j < acols; j += 32) {
+      auto w_of = [&](int j) {
         const int sl = g * acols + j;
         T d0 = T(0), d1 = T(0);
         int gg = 0;
@@ -272,19 +273,12 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
           d1 += part[(gg + 1) * ucols + sl];
         }
         if (gg < rg) d0 += part[gg * ucols + sl];
-        const int c = k + 1 + j;
-        const double w = fma(sk, (double)(d0 + d1), (double)col(g, 0, c)[k]);
-        const T cf = (T)(tk * w), cs = (T)(ts * w);
-        coef[g * n + c] = cf;
-        cscl[g * n + c] = cs;
-        if (j == 0) {
-          cf1 = cf;
-          cs1 = cs;
-        }
-      }
-      if (acols > 0) {
-        cf1 = __shfl_sync(0xffffffffu, cf1, 0);
-        cs1 = __shfl_sync(0xffffffffu, cs1, 0);
+        return fma(sk, (double)(d0 + d1), (double)col(g, 0, k + 1 + j)[k]);
+      };
+      if (warp <= G) {
+        const double w = w_of(0);
+        const T cf1 = (T)(tk * w), cs1 = (T)(ts * w);
+        __syncwarp();
         if (lane == 0) col(g, 0, k + 1)[k] -= cf1;
         double ss = 0.0;
 #pragma unroll
@@ -303,9 +297,15 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
         if (lane == 0) ssq[g] = ss;
+      } else {
+        for (int j = 1 + lane; j < acols; j += 32) {
+          const double w = w_of(j);
+          coef[g * n + k + 1 + j] = (T)(tk * w);
+          cscl[g * n + k + 1 + j] = (T)(ts * w);
+        }
       }
-    } else if (kBuildT && warp > G) {
-      for (int zs = tid - 32 * (G + 1); zs < zcols; zs += NT - 32 * (G + 1)) {
+    } else if (kBuildT && warp > 2 * G) {
+      for (int zs = tid - 32 * (2 * G + 1); zs < zcols; zs += NT - 32 * (2 * G + 1)) {
         const int np = npairs > 0 ? npairs : 1;
         const int g = zs / np, t = zs % np;
         T d1 = T(0), d2 = T(0);

@@ -24,7 +24,7 @@ constexpr int kApplyRows = 32;
 // Largest n the kernels are built for.
 constexpr int kMaxN = 128;
 // Largest leaf height and panel width of the BF16x3 tensor-core leaf update.
-constexpr int kBf16x3MaxLeaf = 256;
+constexpr int kBf16x3MaxLeaf = 512;
 constexpr int kBf16x3MaxN = 64;
 
 // Three apply modes: C <- Q^T C, C <- Q C, and "form": C <- Q [X; 0] where X
