@@ -260,9 +260,14 @@ def caqr_run(tq, torch, args, steps, warmup, dtype=None, upd=None):
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
         ach = 3 * upd_flops / (upd_ms / 1e3) / 1e12
+        # C (FP32) is read twice and written once per panel: 12 bytes per element.
+        upd_bytes = sum(12.0 * (n - j) * (n - j - b) for j in range(0, n, b))
         roof = {"bound": "tensor", "kernel": "bf16x3_update_kernel (tcgen05, 3 BF16 products per FP32 product)",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "note": "achieved counts the 3 BF16 products; the trailing matrix is re-read per panel, so HBM binds at b = 64"}
+                "hbm_achieved_gbs": upd_bytes / (upd_ms / 1e3) / 1e9,
+                "note": "achieved counts the 3 BF16 products; at b = 64 the update is bound neither by the "
+                        "tensor pipe nor by HBM but by each CTA's serial stage / MMA / epilogue steps; the "
+                        "CAQR total is set by the panel chain (leaf and tree factor of each panel)"}
     elif upd == tq.PREC_FP32:
         ach = upd_flops / (upd_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": "leaf_apply_kernel<float> (trailing update)", "achieved": ach,

@@ -430,7 +430,9 @@ size_t node_apply_smem(int n, int q, size_t elem) {
 // CTAs, units = w S + f, and the last f units run as a partial wave.  Cut
 // into p column pieces they take ceil(p f / S) / p of a wave instead of one
 // (each piece costs a little more than its share: Y and T are staged again).
-// Returns p (1: no split) and the first unit that is split.
+// p goes up to pmax, and to 4 whenever the 4 f pieces all run at once (then
+// a piece's lower per-SM efficiency costs nothing).  Returns p (1: no
+// split) and the first unit that is split.
 template <typename K>
 int tail_split(K kern, size_t smem, int64_t units, int pmax, int64_t* split_from) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -441,7 +443,8 @@ int tail_split(K kern, size_t smem, int64_t units, int pmax, int64_t* split_from
   const int64_t f = units % S;
   int split = 1;
   double best = 1.0;
-  for (int p = 2; f > 0 && p <= pmax; p *= 2) {
+  for (int p = 2; f > 0 && p <= 4; p *= 2) {
+    if (p > pmax && (int64_t)p * f > S) break;
     const double t = (double)((p * f + S - 1) / S) / p + 0.04 * (p - 1);
     if (t < best) {
       best = t;
@@ -461,8 +464,9 @@ cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int64_t kchunks = (a.k + kApplyCols - 1) / kApplyCols;
   const int64_t units = a.nleaves * kchunks;
-  // Quarter pieces (16 columns) only in form mode: in the apply modes
-  // W = Y^T C runs over all h rows, and 16 columns give it two warps per CTA.
+  // Quarter pieces (16 columns) in the apply modes only when they all fit in
+  // one round: there W = Y^T C runs over all h rows, and 16 columns give it
+  // two warps per CTA.
   LeafApplyArgs<T> b = a;
   b.split = tail_split(kern, smem, units, a.mode == kApplyForm ? 4 : 2, &b.split_from);
   const int64_t grid = b.split_from + (units - b.split_from) * b.split;

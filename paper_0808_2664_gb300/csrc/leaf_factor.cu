@@ -1,25 +1,17 @@
 // Leaf Householder QR of every row block of A (Section 2.1,
 // Eq. TSQR_binarytree_1: A_i = Q_i R_i for each block A_i).
 //
-// One CTA factors one leaf at a time (grid-stride over leaves); several CTAs
-// share an SM so that one CTA's serial reflector step overlaps the others'
-// bulk updates.  The h x n leaf sits in shared memory, column-major with an
-// odd leading dimension so that threads walking different columns at the
-// same row hit different banks.  Per column j:
-//   C  one warp computes the squared norm of the tail (all 32 lanes, FP64),
-//      its lane 0 turns (alpha, ||tail||^2) into (beta, tau, scale), and the
-//      warp scales the tail into the Householder vector u_j (unit entry
-//      implicit);
-//   A  dot products w_c = u_j^T a_c for the trailing columns c > j, rows
-//      split into groups whose partial sums go to shared memory, then one
-//      thread per column sums its partials into tau_j w_c;
-//   B  a_c -= tau_j w_c u_j.
-// Work is re-partitioned over all threads in every phase, so the shrinking
-// active block keeps every warp busy.  After the last column, the
-// compact-WY T of the leaf is built from Z = strictly-upper(Y^T Y) (a
-// register-tiled product) and tau by a blocked doubling recurrence.
-// Arithmetic: products in T (FP64, or FP32 for the mixed form); norms, beta,
-// tau and scale always in FP64.
+// One CTA factors one leaf at a time (grid-stride over leaves).  The h x n
+// leaf sits in shared memory, column-major with an odd leading dimension so
+// that threads walking different columns at the same row hit different
+// banks.  The column schedule (leaf_device.cuh): per column, one warp forms
+// the reflector while the update warps apply the previous reflector to every
+// trailing column fused with that column's dot against the new tail; a short
+// coefficient step and a single-column step follow; a separate group of
+// warps accumulates Z = strictly-upper(Y^T Y) as the tails become final.
+// After the last column the leaf's compact-WY T is built from Z and tau by a
+// blocked doubling recurrence.  Arithmetic: products in the storage type T
+// (FP64, or FP32 for the mixed form); norms, beta, tau and scale in FP64.
 #include <cuda_runtime.h>
 
 #include "leaf_device.cuh"
