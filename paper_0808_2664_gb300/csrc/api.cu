@@ -92,6 +92,11 @@ struct caqr_q_s {
   // trailing matrix is updated on the caller's stream.
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> ev_left, ev_fact;
+  // The FP64 trailing update of a wide panel is issued as two column halves
+  // on the caller's stream and on `upd2`, so that one half's latency-bound
+  // tree levels overlap the other half's leaf blocks.
+  cudaStream_t upd2 = nullptr;
+  std::vector<cudaEvent_t> ev_fork, ev_join;
   int32_t upd = TSQR_PREC_FP64;  // trailing-update arithmetic
   // caqr_refactor's panel loop as a CUDA graph, captured for one (A, lda)
   // on a private stream and replayed on the caller's stream.
@@ -804,11 +809,16 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
         cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi) != cudaSuccess)
       rc = TSQR_ERR_CUDA;
   }
+  if (rc == TSQR_OK && cudaStreamCreateWithFlags(&c->upd2, cudaStreamNonBlocking) != cudaSuccess) rc = TSQR_ERR_CUDA;
   c->ev_left.assign(c->panels.size(), nullptr);
   c->ev_fact.assign(c->panels.size(), nullptr);
+  c->ev_fork.assign(c->panels.size(), nullptr);
+  c->ev_join.assign(c->panels.size(), nullptr);
   for (size_t j = 0; j < c->panels.size() && rc == TSQR_OK; ++j) {
     if (cudaEventCreateWithFlags(&c->ev_left[j], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_fact[j], cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&c->ev_fact[j], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork[j], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join[j], cudaEventDisableTiming) != cudaSuccess)
       rc = TSQR_ERR_CUDA;
   }
   if (rc != TSQR_OK) {
@@ -818,6 +828,10 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
   *q = c;
   return TSQR_OK;
 }
+
+// Column granularity of the two-stream split of a trailing update (a
+// multiple of both update kernels' column chunks).
+constexpr int64_t kUpdateSplitCols = 128;
 
 // Issues the panel loop on s (the caller's stream, or the capture stream).
 static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
@@ -831,6 +845,7 @@ static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
   auto at = [&](int64_t i, int64_t j) -> void* { return (unsigned char*)A + (size_t)(i + j * lda) * es; };
   int rc = refactor(c->panels[0], A, lda, A, lda, false, s);
   if (rc != TSQR_OK) return rc;
+  int64_t joined = -1;  // panel whose second update half the caller's stream has not yet waited for
   for (size_t j = 0; j < np; ++j) {
     tsqr_q_s* p = c->panels[j];
     const int64_t j0 = (int64_t)j * c->b;
@@ -847,11 +862,28 @@ static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
     if (cudaEventRecord(c->ev_fact[j + 1], c->side) != cudaSuccess) return TSQR_ERR_CUDA;
     const int64_t kt = c->n - j1 - nx->n;
     if (kt > 0) {
-      rc = apply_common(p, kApplyQT, kt, at(j0, j1 + nx->n), lda, s);
+      // The previous step's second half may have touched any of these columns.
+      if (joined >= 0 && cudaStreamWaitEvent(s, c->ev_join[joined], 0) != cudaSuccess) return TSQR_ERR_CUDA;
+      joined = -1;
+      // FP64 only (its updates bound the loop; the FP32-storage forms are
+      // bound by the panel chain, which the split slows a little), and not
+      // under stage timing, whose per-stage event times must not overlap.
+      const bool split = c->upd == TSQR_PREC_FP64 && !c->timing && kt >= 8 * kUpdateSplitCols;
+      const int64_t kt1 = split ? (kt / 2 + kUpdateSplitCols - 1) / kUpdateSplitCols * kUpdateSplitCols : kt;
+      if (kt1 < kt) {
+        if (cudaEventRecord(c->ev_fork[j], s) != cudaSuccess) return TSQR_ERR_CUDA;
+        if (cudaStreamWaitEvent(c->upd2, c->ev_fork[j], 0) != cudaSuccess) return TSQR_ERR_CUDA;
+        rc = apply_common(p, kApplyQT, kt - kt1, at(j0, j1 + nx->n + kt1), lda, c->upd2);
+        if (rc != TSQR_OK) return rc;
+        if (cudaEventRecord(c->ev_join[j], c->upd2) != cudaSuccess) return TSQR_ERR_CUDA;
+        joined = (int64_t)j;
+      }
+      rc = apply_common(p, kApplyQT, kt1, at(j0, j1 + nx->n), lda, s);
       if (rc != TSQR_OK) return rc;
     }
     if (cudaStreamWaitEvent(s, c->ev_fact[j + 1], 0) != cudaSuccess) return TSQR_ERR_CUDA;
   }
+  if (joined >= 0 && cudaStreamWaitEvent(s, c->ev_join[joined], 0) != cudaSuccess) return TSQR_ERR_CUDA;
   return TSQR_OK;
 }
 
@@ -1036,6 +1068,14 @@ int caqr_q_destroy(caqr_q_t q) {
     if (e) cudaEventDestroy(e);
   for (auto e : q->ev_fact)
     if (e) cudaEventDestroy(e);
+  for (auto e : q->ev_fork)
+    if (e) cudaEventDestroy(e);
+  for (auto e : q->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (q->upd2) {
+    cudaStreamSynchronize(q->upd2);
+    cudaStreamDestroy(q->upd2);
+  }
   for (auto* p : q->panels) destroy_handle(p);
   cudaError_t e = q->ws ? cudaFree(q->ws) : cudaSuccess;
   if (q->graph) cudaGraphExecDestroy(q->graph);
