@@ -199,6 +199,11 @@ int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t lda, double* 
  * For panel j the trailing columns receive (Q_j D_j)^T: first the leaf
  * blocks, then the tree nodes on stacked b-row slices (Section 3.1), then
  * the panel's signs, so rows of R stay consistent without a later fix.
+ * The next panel is factored on a handle-owned stream of the highest
+ * priority while the rest of the trailing matrix is updated, and in FP64
+ * half of each wide trailing update runs on a second handle-owned stream;
+ * both join the caller's stream, so the call is complete when the work it
+ * queued there is.  Calls with the same handle must not overlap.
  */
 int caqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int64_t b, int32_t update_precision,
                 const tsqr_opts_t* opts, caqr_q_t* q, tsqr_stream_t stream);

@@ -37,7 +37,9 @@
 
 namespace tsqr {
 
-constexpr int kNode2MaxGroups = 4;  // row groups per column in the update phase
+// Row groups per column in the update phase: four for 256 threads, eight
+// for the 512-thread form used on narrow levels (shorter per-item chains).
+__host__ __device__ constexpr int node2_max_groups(int nt) { return nt >= 512 ? 8 : 4; }
 constexpr int kNode2MinRows = 4;    // rows per group at least
 
 __host__ __device__ inline int node2_packed(int n) { return n * (n + 1) / 2; }
@@ -161,7 +163,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
       int byrows = (k + 1) / kNode2MinRows;
       if (byrows < 1) byrows = 1;
       if (rg > byrows) rg = byrows;
-      if (rg > kNode2MaxGroups) rg = kNode2MaxGroups;
+      if (rg > node2_max_groups(NT)) rg = node2_max_groups(NT);
       if (rg < 1) rg = 1;
     }
     const int ucols = G * acols, zcols = G * npairs;

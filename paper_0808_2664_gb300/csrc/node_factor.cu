@@ -80,11 +80,16 @@ cudaError_t launch_node_factor(const NodeFactorArgs<T>& a, cudaStream_t s) {
     // their tiles fit); narrow binary levels (fewer groups than about two per
     // SM) and arity 4: one node per CTA, three CTAs per SM at n = 64 (measured
     // faster for the four-triangle nodes, whose steps are three times wider).
+    // Levels with at most one node per SM run 512-thread CTAs: the same
+    // serial steps, twice the warps (and row groups) for the update items.
+    const bool narrow = a.nodes <= (int64_t)sms;
     if (a.arity == 2) {
       const bool wide = a.nodes >= 4 * (int64_t)sms;
       if (wide && node2_smem_bytes(a.n, 2, sizeof(T), 256, 2) <= (size_t)smax) return launch_node2<T, 256, 2, 2>(a, sms, s);
+      if (narrow && node2_smem_bytes(a.n, 1, sizeof(T), 512, 2) <= (size_t)smax) return launch_node2<T, 512, 1, 2>(a, sms, s);
       return launch_node2<T, 256, 1, 2>(a, sms, s);
     }
+    if (narrow && node2_smem_bytes(a.n, 1, sizeof(T), 512, 4) <= (size_t)smax) return launch_node2<T, 512, 1, 4>(a, sms, s);
     return launch_node2<T, 256, 1, 4>(a, sms, s);
   }
   // Arity 8 and 16 (short trees over few leaves, e.g. CAQR panels): the

@@ -79,7 +79,8 @@ def test_factor_and_form_q_match_oracle(oracle_mod, dtype, m, n, h, q):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("m,n,h,q", [(4096, 32, 256, 2), (1000, 7, 64, 2), (5000, 16, 128, 4), (3000, 128, 128, 2)])
+@pytest.mark.parametrize("m,n,h,q", [(4096, 32, 256, 2), (1000, 7, 64, 2), (5000, 16, 128, 4), (3000, 128, 128, 2),
+                                     (20000, 16, 64, 8)])
 def test_apply_qt_and_apply_q(oracle_mod, dtype, m, n, h, q):
     if dtype == torch.float64 and n > 64:
         pytest.skip("FP64 n > 64 is served by caqr_factor")
