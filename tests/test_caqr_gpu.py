@@ -35,6 +35,7 @@ def host(t):
     (3000, 128, 64, 0),    # tall n = 128 in FP64 via two 64-column panels
     (300, 300, 7, 64),     # odd panel width
     (120, 120, 120, 0),    # one panel: CAQR reduces to TSQR
+    (1300, 1200, 64, 0),   # wide trailing updates: two column halves on two streams
 ])
 def test_caqr_matches_oracle(oracle_mod, m, n, b, h):
     A = inputs.uniform(m, n, seed=3000 + m + n)
@@ -86,7 +87,7 @@ def test_caqr_argument_errors():
 def test_refactor_graph_replay_matches_direct(prec):
     """caqr_refactor's captured panel loop gives bitwise the direct loop's result,
     on replay, on a second buffer (a new capture) and with stage timing on (direct)."""
-    m, n, b = 1500, 700, 64
+    m, n, b = 1500, 1280, 64  # the first FP64 trailing updates are wide enough to split
     A = inputs.uniform(m, n, seed=3500)
     dt = torch.float64 if prec == "fp64" else torch.float32
     upd = {"fp64": tq.PREC_FP64, "fp32": tq.PREC_FP32, "bf16x3": tq.UPDATE_BF16X3}[prec]
