@@ -23,7 +23,8 @@ constexpr int kApplyCols = 64;
 constexpr int kApplyRows = 32;
 // Largest n the kernels are built for.
 constexpr int kMaxN = 128;
-// Largest leaf height and panel width of the BF16x3 tensor-core leaf update.
+// Leaf height cap of CAQR panels with BF16x3 tensor-core updates (the
+// update kernel takes any height), and its largest panel width.
 constexpr int kBf16x3MaxLeaf = 512;
 constexpr int kBf16x3MaxN = 64;
 
