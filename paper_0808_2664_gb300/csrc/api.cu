@@ -168,9 +168,12 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     // tree's work is about n / (2h) of the leaves') and a smaller n^3 share
     // in forming Q, at one leaf CTA per SM.
     // FP32 leaves stop at 512 rows: beyond that the shorter tree no longer
-    // pays for the longer serial leaf (measured at n = 64 and 128).
+    // pays for the longer serial leaf (measured at n = 64 and 128); at
+    // n <= 64 they stop at 384, whose tile (under 100 KB) lets two CTAs share
+    // an SM and overlap their serial column steps (measured at n = 64: 21.2
+    // against 22.1 ms for 512 rows).
     h = smax / (int64_t)q->es / n / 32 * 32;
-    const int64_t hcap = q->es == 8 ? 1024 : 512;
+    const int64_t hcap = q->es == 8 ? 1024 : (n <= 64 ? 384 : 512);
     if (h > hcap) h = hcap;
     if (h < n) h = n;
   }
@@ -766,10 +769,11 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
     }
     // Panels take the plain TSQR default (the tallest leaf that fits): the
     // tree part of each trailing update is about n / h of its leaf part.
-    // BF16x3 panels: power-of-two leaves of at most kBf16x3MaxLeaf rows
-    // (512 at b = 64 in FP32: two tree levels per 8192-row panel).
+    // FP32-storage panels: power-of-two leaves of at most kBf16x3MaxLeaf
+    // rows (512 at b = 64: two tree levels per 8192-row panel, whose chain
+    // of leaf and tree latencies bounds these forms).
     tsqr_opts_t po = opts ? *opts : tsqr_opts_t{0, 0, 0};
-    if (po.leaf_rows == 0 && update_precision == TSQR_UPDATE_BF16X3) {
+    if (po.leaf_rows == 0 && c->prec == TSQR_PREC_FP32) {
       int64_t h = 1;
       while (h * 2 <= (160 * 1024 / (int64_t)c->es) / jb && h * 2 <= kBf16x3MaxLeaf) h *= 2;
       po.leaf_rows = h < jb ? jb : h;

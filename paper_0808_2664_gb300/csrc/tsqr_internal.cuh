@@ -23,8 +23,8 @@ constexpr int kApplyCols = 64;
 constexpr int kApplyRows = 32;
 // Largest n the kernels are built for.
 constexpr int kMaxN = 128;
-// Leaf height cap of CAQR panels with BF16x3 tensor-core updates (the
-// update kernel takes any height), and its largest panel width.
+// Leaf height cap of CAQR panels with FP32 storage (the BF16x3 update
+// kernel takes any height), and the BF16x3 update's largest panel width.
 constexpr int kBf16x3MaxLeaf = 512;
 constexpr int kBf16x3MaxN = 64;
 
