@@ -22,6 +22,9 @@ What each function computes, and the paper passage it follows:
   paper cites for the local QR (Section 2.1, last paragraph).
 * ``qr_backward`` -- the QR adjoint for a differentiable TSQR (not in the
   paper; it is the standard adjoint of the sign-normalised thin QR).
+* ``lstsq`` -- least-squares solutions and residual norms through the same
+  Householder QR (Section 1: the tall-skinny least-squares problem TSQR
+  serves): Q^T B, then back substitution with R.
 
 Pins (``tests/test_oracle.py``): closed forms for 2x2 and 3x2 inputs, exact
 rational QR of tiny integer matrices, R^T R = A^T A via an independent
@@ -75,9 +78,10 @@ def _load():
             lib.oracle_larft.argtypes = [i64, i64, dp, i64, dp, dp, i64]
             lib.oracle_qr.argtypes = [i64, i64, dp, i64, dp, i64, dp, dp, dp, i64, dp, i64]
             lib.oracle_qr_backward.argtypes = [i64, i64, dp, dp, dp, dp, dp]
+            lib.oracle_lstsq.argtypes = [i64, i64, dp, i64, i64, dp, i64, dp, i64, dp]
             lib.oracle_num_threads.restype = ctypes.c_int
             for f in (lib.oracle_geqr2, lib.oracle_extract_r, lib.oracle_apply_qt, lib.oracle_apply_q,
-                      lib.oracle_form_q, lib.oracle_larft, lib.oracle_qr, lib.oracle_qr_backward):
+                      lib.oracle_form_q, lib.oracle_larft, lib.oracle_qr, lib.oracle_qr_backward, lib.oracle_lstsq):
                 f.restype = None
             _lib = lib
     return _lib
@@ -186,6 +190,24 @@ def qr_backward(Q, R, dQ, dR) -> np.ndarray:
     dA = np.zeros((m, n), order="F")
     lib.oracle_qr_backward(m, n, _p(Q), _p(R), _p(dQ), _p(dR), _p(dA))
     return dA
+
+
+def lstsq(A, B):
+    """(X, rnorm): X (n x k) minimises ||A X - B||_F column by column; rnorm[c] = ||A x_c - b_c||_2."""
+    lib = _load()
+    A = _f64(A)
+    B = _f64(B)
+    if B.ndim == 1:
+        B = B[:, None]
+    B = np.asfortranarray(B)
+    m, n = A.shape
+    k = B.shape[1]
+    if B.shape[0] != m or m < n:
+        raise ValueError("lstsq needs A m x n with m >= n and B with m rows")
+    X = np.zeros((n, k), order="F")
+    rn = np.zeros(k)
+    lib.oracle_lstsq(m, n, _p(A), max(m, 1), k, _p(B), max(m, 1), _p(X), max(n, 1), _p(rn))
+    return X, rn
 
 
 def num_threads() -> int:

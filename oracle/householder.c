@@ -35,7 +35,10 @@
  * bound argument), LAPACK QR run as a library, orthogonality and residual
  * bounds, and row-permutation / tree-shape invariance.  The T factor of the
  * compact WY form is pinned against the explicit product of reflectors; the
- * QR adjoint is pinned by central finite differences.  Intermediate tree data
+ * QR adjoint is pinned by central finite differences; least squares by the
+ * closed-form straight-line fit, the normal equations A^T (A x - b) = 0, exact
+ * recovery of consistent systems and LAPACK's least-squares solver run as a
+ * library.  Intermediate tree data
  * (Y, tau, T of a given tree) are not part of any pin: they depend on the tree.
  */
 #include <math.h>
@@ -244,6 +247,39 @@ void oracle_qr_backward(int64_t m, int64_t n, const double* Q, const double* R, 
   }
   free(M);
   free(S);
+}
+
+/*
+ * Least squares min ||A x_c - b_c||_2 for the k columns of B (Section 1: the
+ * tall-skinny least-squares problem that TSQR serves), the textbook way:
+ * Householder QR of a copy of A (oracle_geqr2), Q^T B by H_0, ..., H_{n-1} in
+ * order (no sign normalisation: R and Q^T B then carry the same signs), back
+ * substitution with R = triu(A(0:n, 0:n)) for X (n x k, ldx), and the
+ * residual norms rnorm[c] = ||(Q^T b_c)(n:m)||_2 (scaled norm).  A zero
+ * diagonal entry of R (rank-deficient A) gives inf or NaN in X.
+ */
+void oracle_lstsq(int64_t m, int64_t n, const double* A, int64_t lda, int64_t k, const double* B, int64_t ldb,
+                  double* X, int64_t ldx, double* rnorm) {
+  double* Y = (double*)malloc(sizeof(double) * (size_t)(m * n > 0 ? m * n : 1));
+  double* tau = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* C = (double*)malloc(sizeof(double) * (size_t)(m * k > 0 ? m * k : 1));
+  for (int64_t c = 0; c < n; ++c) memcpy(&Y[IDX(0, c, m)], &A[IDX(0, c, lda)], sizeof(double) * (size_t)m);
+  for (int64_t c = 0; c < k; ++c) memcpy(&C[IDX(0, c, m)], &B[IDX(0, c, ldb)], sizeof(double) * (size_t)m);
+  oracle_geqr2(m, n, Y, m, tau);
+  for (int64_t j = 0; j < n; ++j) apply_reflector(m, j, Y, m, tau[j], k, C, m);
+  for (int64_t c = 0; c < k; ++c) {
+    double* x = &X[IDX(0, c, ldx)];
+    const double* y = &C[IDX(0, c, m)];
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int64_t j = i + 1; j < n; ++j) s -= Y[IDX(i, j, m)] * x[j];
+      x[i] = s / Y[IDX(i, i, m)];
+    }
+    if (rnorm) rnorm[c] = scaled_nrm2(y + n, m - n);
+  }
+  free(Y);
+  free(tau);
+  free(C);
 }
 
 /* Number of OpenMP threads the oracle would use (1 without OpenMP). */

@@ -251,3 +251,51 @@ def test_qr_backward_finite_differences(oracle_mod):
         fd = (loss(A + h * E) - loss(A - h * E)) / (2 * h)
         an = float(np.sum(dA * E))
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (fd, an)
+
+
+# ------------------------------------------------------------ least squares --
+def test_lstsq_straight_line_closed_form(oracle_mod):
+    """Fit y = x0 + x1 t through (0, 1), (1, 2), (2, 4): the normal equations
+    [[3, 3], [3, 5]] x = [7, 10] give x = (5/6, 3/2), residual (1, -2, 1)/6."""
+    A = np.array([[1.0, 0.0], [1.0, 1.0], [1.0, 2.0]])
+    b = np.array([1.0, 2.0, 4.0])
+    X, rn = oracle_mod.lstsq(A, b)
+    np.testing.assert_allclose(X[:, 0], [5.0 / 6.0, 1.5], rtol=0, atol=8 * EPS64)
+    assert abs(rn[0] - math.sqrt(6.0) / 6.0) <= 8 * EPS64
+
+
+def test_lstsq_regression_formula(oracle_mod):
+    """Simple linear regression: slope = sum (t - tm)(y - ym) / sum (t - tm)^2, intercept = ym - slope tm."""
+    rng = np.random.default_rng(17)
+    t = rng.uniform(-3, 3, 50)
+    y = 0.7 - 1.3 * t + 0.1 * rng.standard_normal(50)
+    A = np.stack([np.ones_like(t), t], axis=1)
+    X, rn = oracle_mod.lstsq(A, y)
+    tm, ym = t.mean(), y.mean()
+    slope = np.sum((t - tm) * (y - ym)) / np.sum((t - tm) ** 2)
+    icept = ym - slope * tm
+    np.testing.assert_allclose(X[:, 0], [icept, slope], rtol=1e-13)
+    assert abs(rn[0] - np.linalg.norm(y - icept - slope * t)) <= 1e-13 * np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("m,n,k", [(300, 7, 3), (2000, 40, 5), (64, 64, 2)])
+def test_lstsq_normal_equations_and_lapack(oracle_mod, m, n, k):
+    A = inputs.gaussian(m, n, 500 + n)
+    B = inputs.gaussian(m, k, 600 + n)
+    X, rn = oracle_mod.lstsq(A, B)
+    Rres = A @ X - B
+    # The residual is orthogonal to range(A) (the normal equations).
+    assert np.abs(A.T @ Rres).max() <= fp64_tol(m, n) * np.linalg.norm(A) * np.linalg.norm(B)
+    np.testing.assert_allclose(rn, np.linalg.norm(Rres, axis=0), rtol=fp64_tol(m, n), atol=fp64_tol(m, n))
+    Xl = np.linalg.lstsq(A, B, rcond=None)[0]  # LAPACK, run as a library
+    kappa = np.linalg.cond(A)
+    assert np.abs(X - Xl).max() <= fp64_tol(m, n) * kappa * kappa * np.abs(Xl).max()
+
+
+def test_lstsq_consistent_system_recovered(oracle_mod):
+    m, n = 500, 12
+    A = inputs.gaussian(m, n, 701)
+    Xt = inputs.gaussian(n, 3, 702)
+    X, rn = oracle_mod.lstsq(A, A @ Xt)
+    np.testing.assert_allclose(X, Xt, rtol=0, atol=fp64_tol(m, n) * np.linalg.cond(A) * np.abs(Xt).max())
+    assert np.all(rn <= fp64_tol(m, n) * np.linalg.norm(A @ Xt, axis=0))
