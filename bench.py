@@ -56,7 +56,19 @@ def parse():
     p.add_argument("--caqr-arity", type=int, default=0, help="0 = the library default")
     p.add_argument("--caqr-n", type=int, default=8192, help="square CAQR size for the CAQR variant")
     p.add_argument("--caqr-b", type=int, default=64)
+    p.add_argument("--peaks", action="store_true",
+                   help="compile and run bench_peaks.cu (FP64 / FP32 FMA and DMMA throughput probes) and exit")
     return p.parse_args()
+
+
+def run_peaks():
+    """FP64 FMA, FP32 FMA and DMMA rates of this GPU (bench_peaks.cu), printed as its own lines."""
+    import tempfile
+
+    exe = os.path.join(tempfile.mkdtemp(prefix="bench_peaks"), "bench_peaks")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
+                    os.path.join(ROOT, "bench_peaks.cu")], check=True)
+    subprocess.run([exe], check=True)
 
 
 def dist_env():
@@ -550,6 +562,9 @@ def ours(args, world, rank, local):
 
 def main():
     args = parse()
+    if args.peaks:
+        run_peaks()
+        return
     world, rank, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, world, rank)

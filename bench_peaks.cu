@@ -1,8 +1,10 @@
-// Throughput probes for the roofline denominators that are not in the
-// driver's measured peaks: FP64 FMA, FP32 FMA and FP64 mma.sync m8n8k4
-// (DMMA) rates, each from independent FMA chains over a full grid, timed with
-// CUDA events.  Build and run:
-//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o peak_probe peak_probe.cu && ./peak_probe
+// Throughput probes for the roofline denominators that MEASURED_PEAKS.json
+// does not hold: FP64 FMA, FP32 FMA and FP64 mma.sync m8n8k4 (DMMA) rates,
+// each from independent FMA chains over a full grid, timed with CUDA events.
+// The benchmark's FP64 roofline is derived from unit counts and clocks; these
+// rates show how close a plain FMA loop gets to it.  Build and run with
+// `python bench.py --peaks`, or:
+//   nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/bench_peaks bench_peaks.cu && /tmp/bench_peaks
 #include <cstdio>
 #include <cuda_runtime.h>
 #define CK(x) do{cudaError_t e=(x); if(e!=cudaSuccess){printf("CUDA %s @%d\n",cudaGetErrorString(e),__LINE__); return 1;}}while(0)

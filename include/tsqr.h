@@ -66,11 +66,33 @@ enum tsqr_precision {
                              accumulated in FP32; FP64 norms, vectors, tau */
 };
 
+/* Bits of tsqr_opts_t.flags (TSQR handles only; CAQR takes update_precision instead). */
+enum tsqr_flags {
+  /* FP32 handles with n <= 64: the leaf stage of tsqr_apply_qt (Q^T C, the
+     trailing-update product of Section 3.1) runs on the tensor cores as three
+     BF16 products per FP32 product, accumulated in FP32, like CAQR's
+     TSQR_UPDATE_BF16X3.  Other handles: TSQR_ERR_UNSUPPORTED. */
+  TSQR_FLAG_APPLY_BF16X3 = 1,
+  /* Hybrid reduction tree (Section 2.1: the flat tree inside a processor,
+     a q-ary tree across processors): the leaves are cut into chains of
+     consecutive leaves, one chain per resident CTA; each chain is a flat
+     tree -- its first leaf an ordinary leaf QR, every later leaf i the QR of
+     [R; A_i] with the chain's running R -- and the q-ary tree (arity from
+     opts) runs over the chains' R factors.  Leaves are n rows shorter than
+     the default so that the stacked tile fits; every leaf keeps its
+     Householder vectors in A (dense for the stacked steps) and its T.
+     Not with TSQR_FLAG_APPLY_BF16X3 or tsqr_factor_form_host. */
+  TSQR_FLAG_HYBRID_TREE = 2,
+  /* Flat tree (Section 2.1's sequential TSQR, Eq. TSQR_seq_runtime): one
+     chain over all leaves, one CTA streams the whole matrix. */
+  TSQR_FLAG_FLAT_TREE = 4
+};
+
 /* Tuning knobs; a zero field means "choose automatically". */
 typedef struct tsqr_opts_s {
   int64_t leaf_rows; /* nominal leaf height h (>= n); rows per leaf block (Section 2.1) */
   int32_t arity;     /* reduction-tree arity q >= 2 (Section 2.1: any tree is valid) */
-  int32_t flags;     /* reserved, must be 0 */
+  int32_t flags;     /* 0 or TSQR_FLAG_* bits; unknown bits are an argument error */
 } tsqr_opts_t;
 
 /* ---------------------------------------------------------------- TSQR -- */
@@ -162,6 +184,76 @@ int tsqr_sync_status(tsqr_q_t q, tsqr_stream_t stream);
 int tsqr_q_info(tsqr_q_t q, int64_t* m, int64_t* n, int32_t* precision, int64_t* leaves,
                 int64_t* leaf_rows, int32_t* arity, int32_t* levels);
 
+/* ------------------------------------------------------ least squares -- */
+
+/*
+ * tsqr_lstsq: least-squares solutions X = argmin ||A X - B||_F of the
+ * factored A (m x n, full column rank) for k right-hand sides, the use of
+ * TSQR that Section 1 starts from, with the square Q applied as its tree:
+ *     Q^T B = [C; D],   X = R^{-1} C,   ||A x_j - b_j||_2 = ||D(:, j)||_2.
+ *   q     : handle of A from tsqr_factor / tsqr_refactor (not destroyed).
+ *   R     : device, the n x n R of that factorisation (ldr >= n).
+ *   B     : device, m x k (ldb >= m), overwritten by Q^T B.
+ *   X     : device, n x k (ldx >= n), receives the solutions; may not alias B.
+ *   rnorm : device array of k entries receiving the residual norms, or NULL.
+ * Element type: the handle's.  A zero or non-finite diagonal entry of R
+ * (rank-deficient A) latches TSQR_ERR_NONFINITE in the handle's status.
+ * rnorm needs k <= 65535 and k doubles of stream-ordered temporary memory
+ * (cudaMallocAsync); FP64 sums of squares (entries beyond about 1e150 in
+ * magnitude overflow).  Asynchronous on `stream`.
+ */
+int tsqr_lstsq(tsqr_q_t q, const void* R, int64_t ldr, int64_t k, void* B, int64_t ldb, void* X, int64_t ldx,
+               void* rnorm, tsqr_stream_t stream);
+
+/*
+ * tsqr_solve_r: X <- R^{-1} X for upper-triangular R (n x n, n <= 128,
+ * ldr >= n) and X (n x k, ldx >= n), device arrays of `precision`
+ * (TSQR_PREC_FP64 or TSQR_PREC_FP32), by back substitution on the device.
+ * With the R-only variant of least squares that Section 1 mentions -- factor
+ * [A, B] and keep only R = [R11, R12; 0, R22] -- the solution is
+ * tsqr_solve_r on R11 and a copy of R12.  status: NULL, or a device int
+ * that receives TSQR_ERR_NONFINITE's bit (value 1) when R has a zero or
+ * non-finite diagonal entry.  Asynchronous on `stream`.
+ */
+int tsqr_solve_r(int64_t n, int64_t k, int32_t precision, const void* R, int64_t ldr, void* X, int64_t ldx,
+                 int* status, tsqr_stream_t stream);
+
+/*
+ * tsqr_column_norms: norms[j] = ||B(:, j)||_2 for the m x k device matrix B
+ * (ldb >= m, k <= 65535), FP64 sums of squares, written in `precision`
+ * (the residual norms of the R-only variant are the column norms of R22).
+ * Uses k doubles of stream-ordered temporary memory.
+ */
+int tsqr_column_norms(int64_t m, int64_t k, int32_t precision, const void* B, int64_t ldb, void* norms,
+                      tsqr_stream_t stream);
+
+/*
+ * tsqr_q_part: copies one stored factor of a leaf or tree node of a factored
+ * handle into `out` (device, caller-owned), asynchronously on `stream`:
+ *   what = TSQR_PART_R   : the node's R before sign normalisation (n x n, ld n,
+ *                          upper triangle; for leaves the leaf R_i of
+ *                          Eq. TSQR_binarytree_1, for level l >= 1 the R of
+ *                          Eqs. TSQR_binarytree_2/3);
+ *          TSQR_PART_T   : its compact-WY T (n x n, ld n, upper triangular):
+ *                          the product of its reflectors is I - Y T Y^T
+ *                          (Schreiber and Van Loan, cited in Section 2.1);
+ *          TSQR_PART_TAU : its n reflector coefficients tau;
+ *          TSQR_PART_Y   : level >= 1 only: the q-1 upper-triangular blocks of
+ *                          its Householder vectors below the unit top block
+ *                          ((q-1) x n x n, each ld n; a leaf's Y is in A).
+ *   level: 0 for leaves, 1..levels for tree levels; index < items on that
+ *   level (with a hybrid tree, level-0 R is per chain, T and tau per leaf).
+ * Elements are in the handle's storage type.  Returns TSQR_ERR_HANDLE for an
+ * unfactored handle, -i for argument i out of range.
+ */
+enum tsqr_part { TSQR_PART_R = 0, TSQR_PART_T = 1, TSQR_PART_TAU = 2, TSQR_PART_Y = 3 };
+int tsqr_q_part(tsqr_q_t q, int32_t what, int32_t level, int64_t index, void* out, tsqr_stream_t stream);
+
+/* tsqr_q_chains: leaves per chain and number of chains (1 and the leaf
+ * count unless the handle was planned with a hybrid or flat tree).  Either
+ * pointer may be NULL. */
+int tsqr_q_chains(tsqr_q_t q, int64_t* leaves_per_chain, int64_t* chains);
+
 /* tsqr_q_destroy: frees the handle and its workspace (after its queued work). */
 int tsqr_q_destroy(tsqr_q_t q);
 
@@ -172,14 +264,17 @@ int tsqr_q_destroy(tsqr_q_t q);
  * running inside another allocator's callback, plugins of frameworks that
  * own all device memory, processes whose memory budget is fixed up front.
  *   Arguments as for tsqr_factor (A is overwritten by the leaf reflectors),
- *   without options or a Q handle: default leaf height, binary tree.
+ *   without options or a Q handle: leaves of a power-of-two height (128
+ *   rows at n = 64), binary tree, R-only kernels (no compact-WY T).
+ *   n > 64 returns TSQR_ERR_UNSUPPORTED.
  *   Workspace comes from one static 64 MiB device array inside the library,
  *   held by every GPU that loads the library until the process exits.
- *   Problems whose tree workspace does not fit (about n*n*8 bytes * 5 per
- *   leaf; at n = 64 with 128-row leaves, m up to roughly 50,000 rows) return
- *   TSQR_ERR_TOO_LARGE without touching the GPU.
- *   The first call on a device looks up the array's address (make it before
- *   any stream capture).  Calls share the array: calls whose GPU work
+ *   Problems whose tree workspace does not fit (about 3 * n*n*8 bytes per
+ *   leaf; at n = 64, m up to roughly 87,000 rows) return TSQR_ERR_TOO_LARGE
+ *   without touching the GPU.
+ *   The first call on a device, and the first after that device's context
+ *   was re-created (cudaDeviceReset), looks up the array's address: make it
+ *   before any stream capture.  Calls share the array: calls whose GPU work
  *   overlaps (other streams, other host threads) race and must be
  *   serialised by the caller.  Device-side conditions are not reported.
  */

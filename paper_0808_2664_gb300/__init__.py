@@ -17,7 +17,7 @@ from ._lib import TsqrBatchOpts, TsqrError, TsqrOpts, check, lib
 
 __all__ = [
     "TsqrError", "QTree", "CaqrQ", "colmajor", "as_colmajor", "tsqr_factor", "tsqr_q_create",
-    "caqr_factor", "caqr_q_create", "Batch", "PREC_FP64", "PREC_FP32", "UPDATE_BF16X3",
+    "caqr_factor", "caqr_q_create", "Batch", "PREC_FP64", "PREC_FP32", "UPDATE_BF16X3", "FLAG_APPLY_BF16X3", "FLAG_HYBRID_TREE", "FLAG_FLAT_TREE", "lstsq", "solve_r", "column_norms",
 ]
 
 PREC_FP64 = 0
@@ -73,8 +73,13 @@ def _stream(t):
     return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
 
 
-def _opts(leaf_rows: int, arity: int):
-    return TsqrOpts(int(leaf_rows), int(arity), 0)
+FLAG_APPLY_BF16X3 = 1
+FLAG_HYBRID_TREE = 2
+FLAG_FLAT_TREE = 4
+
+
+def _opts(leaf_rows: int, arity: int, flags: int = 0):
+    return TsqrOpts(int(leaf_rows), int(arity), int(flags))
 
 
 class QTree:
@@ -102,6 +107,12 @@ class QTree:
                                 ctypes.byref(h), ctypes.byref(q), ctypes.byref(lev)), "tsqr_q_info")
         return {"m": m.value, "n": n.value, "precision": p.value, "leaves": lv.value, "leaf_rows": h.value,
                 "arity": q.value, "levels": lev.value}
+
+    def chains(self) -> dict:
+        """Leaves per chain and chain count (hybrid / flat trees; 1 and the leaf count otherwise)."""
+        L, c = ctypes.c_int64(), ctypes.c_int64()
+        check(lib().tsqr_q_chains(self.ptr, ctypes.byref(L), ctypes.byref(c)), "tsqr_q_chains")
+        return {"leaves_per_chain": L.value, "chains": c.value}
 
     def refactor(self, A, R=None):
         """Factor a new matrix of the handle's shape; no allocation.  Returns R."""
@@ -155,6 +166,45 @@ class QTree:
         self.A = A
         return Q_host, R_host
 
+    def lstsq(self, R, B, X=None, rnorm: bool = True):
+        """Least-squares solutions of the factored A for the columns of B (tsqr_lstsq).
+
+        R: the n x n R of this factorisation; B: m x k column-major, overwritten
+        by Q^T B.  Returns (X, residual norms or None), X n x k."""
+        torch = _torch()
+        if B.dtype != self.dtype or B.shape[0] != self.m:
+            raise ValueError(f"B must be {self.m} x k of dtype {self.dtype}")
+        k = B.shape[1]
+        if X is None:
+            X = colmajor(self.n, k, self.dtype, B.device)
+        rn = torch.empty(k, dtype=self.dtype, device=B.device) if rnorm else None
+        check(lib().tsqr_lstsq(self.ptr, ctypes.c_void_p(R.data_ptr()), _ld(R, "R"), k,
+                               ctypes.c_void_p(B.data_ptr()), _ld(B, "B"), ctypes.c_void_p(X.data_ptr()),
+                               _ld(X, "X"), ctypes.c_void_p(rn.data_ptr()) if rn is not None else None, _stream(B)),
+              "tsqr_lstsq")
+        return X, rn
+
+    PARTS = {"R": 0, "T": 1, "tau": 2, "Y": 3}
+
+    def part(self, what: str, level: int, index: int):
+        """A stored factor of leaf (level 0) or tree node `index` (tsqr_q_part): "R" or "T"
+        (n x n, column-major), "tau" (n) or, for tree levels, "Y" ((q-1) x n x n blocks)."""
+        torch = _torch()
+        n = self.n
+        dev = self.A.device if self.A is not None else "cuda"
+        if what == "tau":
+            out = torch.empty(n, dtype=self.dtype, device=dev)
+        elif what == "Y":
+            q = self.info()["arity"]
+            out = torch.empty((q - 1, n, n), dtype=self.dtype, device=dev)
+        else:
+            out = torch.empty((n, n), dtype=self.dtype, device=dev)
+        check(lib().tsqr_q_part(self.ptr, self.PARTS[what], level, index, ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)), "tsqr_q_part")
+        if what == "Y":
+            return out.transpose(1, 2)  # each block column-major
+        return out if what == "tau" else out.t()
+
     STAGES = ("leaf_factor", "tree_factor", "leaf_apply", "tree_apply")
 
     def set_timing(self, enable: bool = True) -> None:
@@ -185,18 +235,22 @@ class QTree:
             pass
 
 
-def tsqr_q_create(m: int, n: int, dtype=None, device="cuda", leaf_rows: int = 0, arity: int = 0) -> QTree:
-    """Plan and allocate a handle for m x n problems; factor with QTree.refactor."""
+def tsqr_q_create(m: int, n: int, dtype=None, device="cuda", leaf_rows: int = 0, arity: int = 0,
+                  flags: int = 0) -> QTree:
+    """Plan and allocate a handle for m x n problems; factor with QTree.refactor.
+
+    flags: FLAG_APPLY_BF16X3 runs the leaf stage of apply_qt on the tensor
+    cores as three BF16 products (float32 handles, n <= 64)."""
     torch = _torch()
     dtype = dtype or torch.float64
     h = ctypes.c_void_p()
-    o = _opts(leaf_rows, arity)
+    o = _opts(leaf_rows, arity, flags)
     check(lib().tsqr_q_create(m, n, _prec(dtype), ctypes.byref(o), ctypes.byref(h),
                               ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)), "tsqr_q_create")
     return QTree(h, m, n, dtype)
 
 
-def tsqr_factor(A, R=None, leaf_rows: int = 0, arity: int = 0, keep_q: bool = True):
+def tsqr_factor(A, R=None, leaf_rows: int = 0, arity: int = 0, keep_q: bool = True, flags: int = 0):
     """TSQR of the column-major m x n CUDA tensor A (overwritten).  Returns (R, QTree or None)."""
     m, n = A.shape
     lda = _ld(A, "A")
@@ -204,11 +258,61 @@ def tsqr_factor(A, R=None, leaf_rows: int = 0, arity: int = 0, keep_q: bool = Tr
         R = colmajor(n, n, A.dtype, A.device)
     ldr = _ld(R, "R")
     h = ctypes.c_void_p()
-    o = _opts(leaf_rows, arity)
+    o = _opts(leaf_rows, arity, flags)
     fn = lib().tsqr_factor if _prec(A.dtype) == PREC_FP64 else lib().tsqr_factor_f32
     check(fn(m, n, ctypes.c_void_p(A.data_ptr()), lda, ctypes.c_void_p(R.data_ptr()), ldr, ctypes.byref(o),
              ctypes.byref(h) if keep_q else None, _stream(A)), "tsqr_factor")
     return R, (QTree(h, m, n, A.dtype, A) if keep_q and h.value else None)
+
+
+def solve_r(R, X):
+    """X <- R^{-1} X on the device (R upper triangular n x n, X n x k, column-major); returns X."""
+    n, k = X.shape
+    check(lib().tsqr_solve_r(n, k, _prec(X.dtype), ctypes.c_void_p(R.data_ptr()), _ld(R, "R"),
+                             ctypes.c_void_p(X.data_ptr()), _ld(X, "X"), None, _stream(X)), "tsqr_solve_r")
+    return X
+
+
+def column_norms(B):
+    """2-norms of the columns of the column-major CUDA matrix B, computed on the device."""
+    torch = _torch()
+    m, k = B.shape
+    out = torch.empty(k, dtype=B.dtype, device=B.device)
+    check(lib().tsqr_column_norms(m, k, _prec(B.dtype), ctypes.c_void_p(B.data_ptr()), _ld(B, "B"),
+                                  ctypes.c_void_p(out.data_ptr()), _stream(B)), "tsqr_column_norms")
+    return out
+
+
+def lstsq(A, B, adjoined: bool = False, leaf_rows: int = 0, arity: int = 0):
+    """Least squares min ||A X - B|| for the m x n CUDA matrix A and m x k B (neither modified).
+
+    adjoined=False factors A, applies the Q-tree to B and solves with R;
+    adjoined=True is the R-only variant Section 1 mentions: TSQR of [A, B]
+    keeps only R = [R11, R12; 0, R22], X = R11^{-1} R12, and the residual
+    norms are the column norms of R22 (needs n + k within TSQR's width).
+    Returns (X, residual norms)."""
+    torch = _torch()
+    m, n = A.shape
+    k = B.shape[1]
+    if adjoined:
+        W = colmajor(m, n + k, A.dtype, A.device)
+        W[:, :n] = A
+        W[:, n:] = B
+        R, _ = tsqr_factor(W, leaf_rows=leaf_rows, arity=arity, keep_q=False)
+        X = colmajor(n, k, A.dtype, A.device).copy_(R[:n, n:])
+        solve_r(R[:n, :n], X)
+        R22 = colmajor(k, k, A.dtype, A.device).copy_(R[n:, n:])
+        return X, column_norms(R22)
+    W = as_colmajor(A.detach().clone())
+    W = as_colmajor(W)
+    R, q = tsqr_factor(W, leaf_rows=leaf_rows, arity=arity)
+    Bc = colmajor(m, k, B.dtype, B.device).copy_(B)
+    X, rn = q.lstsq(R, Bc)
+    st = q.sync_status()
+    q.destroy()
+    if st != 0:
+        raise TsqrError(st, "lstsq")
+    return X, rn
 
 
 class CaqrQ:

@@ -40,7 +40,13 @@ SIGNATURES = {
     "tsqr_factor_form_host": ([vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp], ctypes.c_int),
     "tsqr_sync_status": ([vp, vp], ctypes.c_int),
     "tsqr_q_info": ([vp, pi64, pi64, pi32, pi64, pi64, pi32, pi32], ctypes.c_int),
+    "tsqr_q_part": ([vp, i32, i32, i64, vp, vp], ctypes.c_int),
+    "tsqr_q_chains": ([vp, pi64, pi64], ctypes.c_int),
+    "tsqr_lstsq": ([vp, vp, i64, i64, vp, i64, vp, i64, vp, vp], ctypes.c_int),
+    "tsqr_solve_r": ([i64, i64, i32, vp, i64, vp, i64, vp, vp], ctypes.c_int),
+    "tsqr_column_norms": ([i64, i64, i32, vp, i64, vp, vp], ctypes.c_int),
     "tsqr_q_destroy": ([vp], ctypes.c_int),
+    "tsqr_test_reflectors": ([i64, vp, vp, i32, vp, vp], ctypes.c_int),
     "tsqr_factor_r_noalloc": ([i64, i64, vp, i64, vp, i64, vp], ctypes.c_int),
     "caqr_factor": ([i64, i64, vp, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),
     "caqr_factor_f32": ([i64, i64, vp, i64, i64, i32, ctypes.POINTER(TsqrOpts), ctypes.POINTER(vp), vp], ctypes.c_int),

@@ -14,15 +14,26 @@ import ctypes
 import torch
 
 from . import PREC_FP32, PREC_FP64, as_colmajor, caqr_factor, colmajor, tsqr_factor
-from ._lib import check, lib
+from ._lib import TsqrError, check, lib
 
 
 def _stream(t):
     return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
 
 
+def _finish(q, where: str) -> None:
+    """Reads the handle's device status (a non-finite column norm or pivot,
+    a bounded wait that gave up) before freeing it; raises on a nonzero one."""
+    st = q.sync_status()
+    q.destroy()
+    if st != 0:
+        raise TsqrError(st, where)
+
+
 def qr_forward(A: torch.Tensor):
-    """(Q, R) of the m x n CUDA tensor A (A itself is not modified)."""
+    """(Q, R) of the m x n CUDA tensor A (A itself is not modified).
+
+    Raises TsqrError when the factorisation met a non-finite value."""
     m, n = A.shape
     W = as_colmajor(A.detach()).clone(memory_format=torch.preserve_format)
     W = as_colmajor(W)
@@ -30,11 +41,11 @@ def qr_forward(A: torch.Tensor):
         q = caqr_factor(W, b=64)
         R = torch.triu(W[:n, :n]).t().contiguous().t()
         Q = q.form_q()
-        q.destroy()
+        _finish(q, "qr_forward (caqr)")
         return Q, R
     R, q = tsqr_factor(W)
     Q = q.form_q()
-    q.destroy()
+    _finish(q, "qr_forward (tsqr)")
     return Q, R
 
 

@@ -50,7 +50,12 @@ struct tsqr_q_s {
   int64_t m = 0, n = 0;
   int64_t h = 0, nleaves = 0, hmax = 0;
   int32_t q = 2, levels = 0;
-  std::vector<int64_t> items;  // items per level; items[0] = leaves
+  std::vector<int64_t> items;  // items per level; items[0] = leaves (chains for the hybrid tree)
+  // Hybrid / flat tree: chains of L consecutive leaves, each a flat tree in
+  // one CTA; the q-ary tree runs over the nchains chain R factors.
+  bool hybrid = false;
+  int64_t L = 1, nchains = 0;
+  int ld_s = 0;  // shared-memory leading dimension of the leaf (or stacked) tile
   // Device workspace (owned unless external).
   unsigned char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -154,8 +159,12 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? TSQR_OK : (e == cudaErro
 // takes what is left and is merged into its predecessor when it would have
 // fewer than n rows.
 int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t* opts) {
-  if (opts && opts->flags != 0) return -4;
+  const int32_t flags = opts ? opts->flags : 0;
+  if (flags & ~(TSQR_FLAG_APPLY_BF16X3 | TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE)) return -4;
   q->prec = prec;
+  q->hybrid = (flags & (TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE)) != 0;
+  // Rows of the stacked tile [R; A_i] beyond the leaf's own rows.
+  const int64_t top = q->hybrid ? n : 0;
   q->es = prec == TSQR_PREC_FP64 ? 8 : 4;
   q->m = m;
   q->n = n;
@@ -175,6 +184,7 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     h = smax / (int64_t)q->es / n / 32 * 32;
     const int64_t hcap = q->es == 8 ? 1024 : (n <= 64 ? 384 : 512);
     if (h > hcap) h = hcap;
+    h -= top;  // hybrid: the stacked tile [R; A_i] must fit
     if (h < n) h = n;
   }
   if (h < n) return -4;
@@ -188,10 +198,11 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     q->hmax = nl > 1 ? (m - (nl - 1) * h > h ? m - (nl - 1) * h : h) : m;
     // An automatic height shrinks until a merged last leaf still fits.
     if (!auto_h || h - 32 < n ||
-        (int64_t)leaf_factor_smem((int)n, leaf_factor_ld((int)q->hmax), q->es) <= smax)
+        (int64_t)leaf_factor_smem((int)n, leaf_factor_ld((int)(q->hmax + top)), q->es) <= smax)
       break;
     h -= 32;
   }
+  q->ld_s = leaf_factor_ld((int)(q->hmax + top));
   q->h = h;
   q->nleaves = nl;
   // Default arity 4 where the four-triangle node fits in shared memory: per
@@ -203,12 +214,30 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     q->q = (int64_t)node_factor_smem((int)n, 4, q->es) <= smax && (int64_t)node_apply_smem((int)n, 4, q->es) <= smax ? 4 : 2;
   }
   if (q->q < 2 || q->q > 16) return -4;
-  q->items.assign(1, nl);
+  if (q->hybrid) {
+    // One chain per resident CTA of the chain kernel (flat tree: one chain).
+    int64_t slots = (flags & TSQR_FLAG_FLAT_TREE) ? 1 : chain_factor_resident((int)n, q->ld_s, q->es);
+    if (slots < 1) slots = 1;
+    q->L = (nl + slots - 1) / slots;
+    q->nchains = (nl + q->L - 1) / q->L;
+    q->items.assign(1, q->nchains);
+  } else {
+    q->L = 1;
+    q->nchains = nl;
+    q->items.assign(1, nl);
+  }
   while (q->items.back() > 1) q->items.push_back((q->items.back() + q->q - 1) / q->q);
   q->levels = (int32_t)q->items.size() - 1;
   if (n > kMaxN) return TSQR_ERR_UNSUPPORTED;
-  if ((int64_t)leaf_factor_smem((int)n, leaf_factor_ld((int)q->hmax), q->es) > smax) return TSQR_ERR_UNSUPPORTED;
+  if (flags & TSQR_FLAG_APPLY_BF16X3) {
+    // Leaf stage of Q^T C on the tensor cores: FP32 storage, at most 64
+    // reflectors, ordinary leaves.
+    if (prec != TSQR_PREC_FP32 || n > kBf16x3MaxN || q->hybrid) return TSQR_ERR_UNSUPPORTED;
+    q->upd = TSQR_UPDATE_BF16X3;
+  }
+  if ((int64_t)leaf_factor_smem((int)n, (int)q->hmax + (int)top, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
   if ((int64_t)leaf_apply_smem((int)n, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
+  if (q->hybrid && (int64_t)chain_apply_smem((int)n, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
   if (q->levels > 0) {
     if ((int64_t)node_factor_smem((int)n, q->q, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
     if ((int64_t)node_apply_smem((int)n, q->q, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
@@ -219,7 +248,7 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
 size_t workspace_bytes(const tsqr_q_s* q) {
   const size_t nn = (size_t)q->n * q->n * q->es, nv = (size_t)q->n * q->es;
   size_t b = 0;
-  b += align_up(q->nleaves * nn) * 2 + align_up(q->nleaves * nv);
+  b += align_up(q->items[0] * nn) + align_up(q->nleaves * nn) + align_up(q->nleaves * nv);
   for (int l = 1; l <= q->levels; ++l) {
     const size_t it = (size_t)q->items[l];
     b += align_up(it * nn) * 2 + align_up(it * (q->q - 1) * nn) + align_up(it * nv);
@@ -237,7 +266,7 @@ void bind_workspace(tsqr_q_s* q, unsigned char* base) {
     return p;
   };
   q->ws = base;
-  q->leafR = take(q->nleaves * nn);
+  q->leafR = take(q->items[0] * nn);  // one R per leaf, or per chain
   q->leafT = take(q->nleaves * nn);
   q->leafTau = take(q->nleaves * nv);
   q->nodeR.assign(q->levels, nullptr);
@@ -259,7 +288,7 @@ void bind_workspace(tsqr_q_s* q, unsigned char* base) {
 void* root_r(const tsqr_q_s* q) { return q->levels == 0 ? q->leafR : q->nodeR[q->levels - 1]; }
 
 int64_t slot_stride(const tsqr_q_s* q, int level) {
-  int64_t s = q->h;
+  int64_t s = q->h * q->L;
   for (int l = 1; l < level; ++l) s *= q->q;
   return s;
 }
@@ -279,7 +308,7 @@ cudaError_t launch_leaf_range(tsqr_q_s* q, T* A, int64_t lda, int64_t l0, int64_
   la.n = (int)q->n;
   la.h = q->h;
   la.nleaves = l1 - l0;
-  la.ld_s = leaf_factor_ld((int)q->hmax);
+  la.ld_s = q->ld_s;
   la.R = (T*)q->leafR + l0 * nn;
   la.tau = (T*)q->leafTau + l0 * q->n;
   la.Tw = (T*)q->leafT + l0 * nn;
@@ -291,9 +320,47 @@ template <typename T>
 cudaError_t run_tree_factor(tsqr_q_s* q, T* R, int64_t ldr, bool zero_lower, cudaStream_t s);
 
 template <typename T>
+ChainApplyArgs<T> chain_apply_args(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc) {
+  ChainApplyArgs<T> ca{};
+  ca.Y = (const T*)q->A;
+  ca.ldy = q->lda;
+  ca.m = q->m;
+  ca.n = (int)q->n;
+  ca.h = q->h;
+  ca.nleaves = q->nleaves;
+  ca.L = q->L;
+  ca.nchains = q->nchains;
+  ca.Tw = (const T*)q->leafT;
+  ca.C = C;
+  ca.ldc = ldc;
+  ca.k = k;
+  ca.mode = mode;
+  return ca;
+}
+
+template <typename T>
 cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
   StageTimer t0(q, TSQR_STAGE_LEAF_FACTOR, s);
-  cudaError_t e = launch_leaf_range(q, A, lda, 0, q->nleaves, s);
+  cudaError_t e;
+  if (q->hybrid) {
+    ChainFactorArgs<T> ca{};
+    ca.A = A;
+    ca.lda = lda;
+    ca.m = q->m;
+    ca.n = (int)q->n;
+    ca.h = q->h;
+    ca.nleaves = q->nleaves;
+    ca.L = q->L;
+    ca.nchains = q->nchains;
+    ca.ld_s = q->ld_s;
+    ca.R = (T*)q->leafR;
+    ca.tau = (T*)q->leafTau;
+    ca.Tw = (T*)q->leafT;
+    ca.status = q->status;
+    e = launch_chain_factor(ca, s);
+  } else {
+    e = launch_leaf_range(q, A, lda, 0, q->nleaves, s);
+  }
   if (e != cudaSuccess) return e;
   t0.stop(1);
   return run_tree_factor(q, R, ldr, zero_lower, s);
@@ -369,6 +436,11 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
     StageTimer t(q, TSQR_STAGE_LEAF_APPLY, s);
     la.mode = md;
     cudaError_t r;
+    if (q->hybrid) {
+      r = launch_chain_apply(chain_apply_args(q, md, k, C, ldc), s);
+      if (r == cudaSuccess) t.stop(1);
+      return r;
+    }
     if constexpr (sizeof(T) == 4) {
       if (md == kApplyQT && q->upd == TSQR_UPDATE_BF16X3)
         r = launch_leaf_update_bf16x3(la, q->status, s);
@@ -665,6 +737,7 @@ int tsqr_factor_form_host(tsqr_q_t q, const void* A_host, int64_t lda_host, void
                           void* R_host, int64_t ldr_host, void* A, int64_t lda, void* Q, int64_t ldq, void* R,
                           int64_t ldr, tsqr_stream_t stream) {
   if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (q->hybrid) return TSQR_ERR_UNSUPPORTED;  // the copies are pipelined by leaf chunks
   const int64_t m = q->m, n = q->n;
   if (!A_host) return -2;
   if (lda_host < m) return -3;
@@ -704,6 +777,76 @@ int tsqr_q_info(tsqr_q_t q, int64_t* m, int64_t* n, int32_t* precision, int64_t*
   if (leaf_rows) *leaf_rows = q->h;
   if (arity) *arity = q->q;
   if (levels) *levels = q->levels;
+  return TSQR_OK;
+}
+
+int tsqr_lstsq(tsqr_q_t q, const void* R, int64_t ldr, int64_t k, void* B, int64_t ldb, void* X, int64_t ldx,
+               void* rnorm, tsqr_stream_t stream) {
+  if (!valid(q) || !q->factored) return TSQR_ERR_HANDLE;
+  if (!R) return -2;
+  if (ldr < q->n) return -3;
+  if (k < 0) return -4;
+  if (k == 0) return TSQR_OK;
+  if (!B) return -5;
+  if (ldb < q->m) return -6;
+  if (!X) return -7;
+  if (ldx < q->n) return -8;
+  if (rnorm && k > 65535) return TSQR_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  // Q^T B (leaves, tree, signs): rows 0..n-1 = Q_thin^T B, the rest carry the residual.
+  int rc = apply_common(q, kApplyQT, k, B, ldb, s);
+  if (rc != TSQR_OK) return rc;
+  const int n = (int)q->n;
+  cudaError_t e = q->prec == TSQR_PREC_FP64
+                      ? launch_solve_upper<double>(n, k, (const double*)R, ldr, (const double*)B, ldb, (double*)X, ldx,
+                                                   q->status, s)
+                      : launch_solve_upper<float>(n, k, (const float*)R, ldr, (const float*)B, ldb, (float*)X, ldx,
+                                                  q->status, s);
+  if (e != cudaSuccess || !rnorm) return cuda_err(e);
+  double* acc = nullptr;
+  if ((e = cudaMallocAsync((void**)&acc, sizeof(double) * k, s)) != cudaSuccess) return TSQR_ERR_NOMEM;
+  e = q->prec == TSQR_PREC_FP64
+          ? launch_column_norms<double>(q->n, q->m, k, (const double*)B, ldb, acc, (double*)rnorm, s)
+          : launch_column_norms<float>(q->n, q->m, k, (const float*)B, ldb, acc, (float*)rnorm, s);
+  const cudaError_t ef = cudaFreeAsync(acc, s);
+  return cuda_err(e != cudaSuccess ? e : ef);
+}
+
+int tsqr_q_part(tsqr_q_t q, int32_t what, int32_t level, int64_t index, void* out, tsqr_stream_t stream) {
+  if (!valid(q) || !q->factored) return TSQR_ERR_HANDLE;
+  if (what < TSQR_PART_R || what > TSQR_PART_Y) return -2;
+  if (level < 0 || level > q->levels || (what == TSQR_PART_Y && level == 0)) return -3;
+  // Level 0: R per leaf (per chain for the hybrid tree), T and tau per leaf.
+  const int64_t count = level == 0 && what != TSQR_PART_R ? q->nleaves : q->items[level];
+  if (index < 0 || index >= count) return -4;
+  if (!out) return -5;
+  const size_t nn = (size_t)q->n * q->n * q->es, nv = (size_t)q->n * q->es;
+  const unsigned char* src = nullptr;
+  size_t bytes = 0;
+  switch (what) {
+    case TSQR_PART_R:
+      src = (const unsigned char*)(level == 0 ? q->leafR : q->nodeR[level - 1]) + index * nn;
+      bytes = nn;
+      break;
+    case TSQR_PART_T:
+      src = (const unsigned char*)(level == 0 ? q->leafT : q->nodeT[level - 1]) + index * nn;
+      bytes = nn;
+      break;
+    case TSQR_PART_TAU:
+      src = (const unsigned char*)(level == 0 ? q->leafTau : q->nodeTau[level - 1]) + index * nv;
+      bytes = nv;
+      break;
+    default:
+      src = (const unsigned char*)q->nodeY[level - 1] + index * (q->q - 1) * nn;
+      bytes = (q->q - 1) * nn;
+  }
+  return cuda_err(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
+int tsqr_q_chains(tsqr_q_t q, int64_t* leaves_per_chain, int64_t* chains) {
+  if (!valid(q)) return TSQR_ERR_HANDLE;
+  if (leaves_per_chain) *leaves_per_chain = q->L;
+  if (chains) *chains = q->nchains;
   return TSQR_OK;
 }
 
@@ -748,6 +891,7 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
   if (update_precision != TSQR_PREC_FP64 && update_precision != TSQR_PREC_FP32 &&
       update_precision != TSQR_UPDATE_BF16X3)
     return -4;
+  if (opts && opts->flags != 0) return -5;
   caqr_q_s* c = new (std::nothrow) caqr_q_s();
   if (!c) return TSQR_ERR_NOMEM;
   c->m = m;
@@ -773,6 +917,7 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
     // rows (512 at b = 64: two tree levels per 8192-row panel, whose chain
     // of leaf and tree latencies bounds these forms).
     tsqr_opts_t po = opts ? *opts : tsqr_opts_t{0, 0, 0};
+    po.flags = 0;  // the trailing-update arithmetic is update_precision
     if (po.leaf_rows == 0 && c->prec == TSQR_PREC_FP32) {
       int64_t h = 1;
       while (h * 2 <= (160 * 1024 / (int64_t)c->es) / jb && h * 2 <= kBf16x3MaxLeaf) h *= 2;

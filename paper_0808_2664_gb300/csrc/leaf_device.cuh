@@ -101,9 +101,18 @@ __device__ __forceinline__ int leaf_groups(int threads, int rows) {
 // (update and dot) is one pass over the trailing block.  A separate group
 // of warps takes the products for T's Z = Y^T Y column by column as the
 // tails become final, off those barriers (see the loop below).
-template <typename T, int NT, int NMAX, bool kWantT = true>
+//
+// Stacked form (kStacked, one step of the flat tree of Section 2.1): the
+// tile is [Rtop; A_i], the n x n upper-triangular R of the previous step
+// (ld n, zeros below the diagonal) over the hl - n rows of Ag.  The same
+// column loop factors it: reflector k then touches row k of Rtop and every
+// row of A_i (the rows of Rtop below row k stay zero in column k), so the
+// Householder vectors are e_k on top and a dense column below; the dense
+// part is written to all hl - n rows of Ag and the new R to Rl (which may be
+// Rtop: Rtop is read before Rl is written).
+template <typename T, int NT, int NMAX, bool kWantT = true, bool kStacked = false>
 __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl, T* taul, T* Tg, int* status,
-                                unsigned char* smem) {
+                                unsigned char* smem, const T* Rtop = nullptr) {
   static_assert(NT >= 128, "the leaf schedule needs at least four warps");
   T* S = reinterpret_cast<T*>(smem);
   unsigned char* aux = smem + leaf_tile_region(n, ld, sizeof(T));
@@ -128,6 +137,11 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
 
   // Load the tile: each thread walks the column-major elements e = tid + t NT,
   // several loads in flight.
+  const int top = kStacked ? n : 0;  // rows of the tile taken from Rtop
+  auto src = [&](int c, int i) -> T {
+    if constexpr (kStacked) return i < n ? Rtop[c * n + i] : Ag[(int64_t)c * lda + (i - n)];
+    else return Ag[(int64_t)c * lda + i];
+  };
   {
     const int total = hl * n;
     int c = tid / hl, i = tid - c * hl;
@@ -140,7 +154,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
       for (int u = 0; u < 4; ++u) {
         cs[u] = c;
         is[u] = i;
-        v[u] = Ag[(int64_t)c * lda + i];
+        v[u] = src(c, i);
         c += dc;
         i += di;
         if (i >= hl) {
@@ -152,7 +166,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
       for (int u = 0; u < 4; ++u) S[cs[u] * ld + is[u]] = v[u];
     }
     for (; e < total; e += NT) {
-      S[c * ld + i] = Ag[(int64_t)c * lda + i];
+      S[c * ld + i] = src(c, i);
       c += dc;
       i += di;
       if (i >= hl) {
@@ -404,10 +418,11 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) Ag[(int64_t)cs[u] * lda + is[u]] = v[u];
+      for (int u = 0; u < 4; ++u)
+        if (is[u] >= top) Ag[(int64_t)cs[u] * lda + (is[u] - top)] = v[u];
     }
     for (; e < total; e += NT) {
-      Ag[(int64_t)c * lda + i] = final_value(c, i);
+      if (i >= top) Ag[(int64_t)c * lda + (i - top)] = final_value(c, i);
       c += dc;
       i += di;
       if (i >= hl) {

@@ -104,6 +104,49 @@ struct NodeApplyArgs {
   int split;
 };
 
+// Hybrid tree: chains of L consecutive leaves, each factored by one CTA as
+// a flat tree (Section 2.1); chain c covers leaves [c L, min((c+1) L, nleaves)).
+template <typename T>
+struct ChainFactorArgs {
+  T* A;             // m x n; leaf rows overwritten with their reflectors
+  int64_t lda;
+  int64_t m;
+  int n;
+  int64_t h;        // rows per leaf (the last leaf runs to m)
+  int64_t nleaves;
+  int64_t L;        // leaves per chain
+  int64_t nchains;
+  int ld_s;         // shared-memory leading dimension (odd, >= rows of a stacked tile)
+  T* R;             // nchains x (n x n): the chains' R factors
+  T* tau;           // nleaves x n
+  T* Tw;            // nleaves x (n x n)
+  int* status;
+};
+
+template <typename T>
+struct ChainApplyArgs {
+  const T* Y;       // the factored A
+  int64_t ldy;
+  int64_t m;
+  int n;
+  int64_t h;
+  int64_t nleaves;
+  int64_t L;
+  int64_t nchains;
+  const T* Tw;      // nleaves x (n x n)
+  T* C;             // m x k
+  int64_t ldc;
+  int64_t k;
+  int mode;         // ApplyMode
+};
+
+template <typename T>
+cudaError_t launch_chain_factor(const ChainFactorArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_chain_apply(const ChainApplyArgs<T>& a, cudaStream_t s);
+size_t chain_apply_smem(int n, size_t elem);
+int chain_factor_resident(int n, int ld, size_t elem);
+
 template <typename T>
 cudaError_t launch_leaf_factor(const LeafFactorArgs<T>& a, cudaStream_t s);
 template <typename T>
@@ -129,6 +172,16 @@ cudaError_t launch_init_form(T* Q, int64_t ldq, int n, const T* d, cudaStream_t 
 // Copy the n x n upper triangle of src (ld n) into dst (ldd), zero below.
 template <typename T>
 cudaError_t launch_copy_upper(const T* src, int n, T* dst, int64_t ldd, cudaStream_t s);
+
+// X = R^{-1} B for upper-triangular R (n <= kMaxN); B may alias X.  A zero or
+// non-finite diagonal entry sets kStatusNonfinite in *status (if non-null).
+template <typename T>
+cudaError_t launch_solve_upper(int n, int64_t k, const T* R, int64_t ldr, const T* B, int64_t ldb, T* X, int64_t ldx,
+                               int* status, cudaStream_t s);
+// out[j] = ||B(r0:m, j)||_2 (FP64 sums of squares in acc, k doubles).
+template <typename T>
+cudaError_t launch_column_norms(int64_t r0, int64_t m, int64_t k, const T* B, int64_t ldb, double* acc, T* out,
+                                cudaStream_t s);
 
 // Shared-memory bytes the leaf factor kernel needs for a leaf of hmax rows.
 size_t leaf_factor_smem(int n, int hmax, size_t elem);

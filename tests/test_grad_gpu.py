@@ -94,3 +94,12 @@ def test_full_size_gradient_against_oracle(oracle_mod, dtype):
     dA_o = oracle_mod.qr_backward(Qh, Rh, dQ.double().cpu().numpy(), dR.double().t().contiguous().t().cpu().numpy())
     got = dA.double().cpu().numpy()
     assert np.linalg.norm(got - dA_o) / np.linalg.norm(dA_o) <= tol * np.linalg.cond(Rh)
+
+
+def test_forward_reports_nonfinite():
+    """A NaN met by the factorisation is read from the handle's status word and raised."""
+    A = inputs.gaussian(2048, 8, 9)
+    A[100, 3] = np.nan
+    with pytest.raises(tq.TsqrError) as ei:
+        tqa.qr_forward(dev(A))
+    assert ei.value.code == 4  # TSQR_ERR_NONFINITE

@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from conftest import fp64_tol
+from conftest import assert_colwise_close, fp64_tol
 from paper_0808_2664_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -40,7 +40,7 @@ def _noalloc_r(A):
     return R.cpu().numpy()
 
 
-@pytest.mark.parametrize("m,n", [(20000, 64), (4096, 32), (1000, 7)])
+@pytest.mark.parametrize("m,n", [(20000, 64), (4096, 32), (1000, 7), (80000, 64)])
 def test_noalloc_matches_tsqr_factor_twice(m, n):
     for seed in (11, 12):  # two calls in a row reuse the same scratch
         A = inputs.gaussian(m, n, seed)
@@ -49,6 +49,26 @@ def test_noalloc_matches_tsqr_factor_twice(m, n):
         ref = R_ref.cpu().numpy()
         assert np.linalg.norm(R - ref) / np.linalg.norm(ref) <= fp64_tol(m, n)
         assert np.array_equal(R, np.triu(R))
+
+
+@pytest.mark.parametrize("m,n", [(3000, 16), (1_300_000, 4)])
+def test_noalloc_matches_oracle(oracle_mod, m, n):
+    """Entry by entry against the CPU oracle's R; the second shape has 1270 leaves of
+    1024 rows, so its first tree level runs hundreds of nodes."""
+    A = inputs.gaussian(m, n, 13)
+    _, Ro = oracle_mod.qr(A, want_q=False)
+    R = _noalloc_r(A)
+    assert np.all(np.diag(R) >= 0)
+    assert_colwise_close(R, Ro, fp64_tol(m, n) * np.linalg.cond(Ro), "R")
+
+
+def test_noalloc_rejects_wide():
+    A = torch.zeros((80, 4000), dtype=torch.float64, device="cuda").t()
+    R = tq.colmajor(80, 80, torch.float64)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib().tsqr_factor_r_noalloc(4000, 80, ctypes.c_void_p(A.data_ptr()), 4000, ctypes.c_void_p(R.data_ptr()),
+                                      80, stream)
+    assert rc == 5  # TSQR_ERR_UNSUPPORTED: n > 64
 
 
 def test_noalloc_rejects_too_large():
