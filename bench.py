@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-variants", action="store_true")
-    p.add_argument("--variants", default="mixed,caqr,caqr_mixed,batched,grad",
+    p.add_argument("--variants", default="mixed,hybrid,lstsq,caqr,caqr_mixed,batched,grad",
                    help="comma list of extra measurements")
     p.add_argument("--caqr-leaf-rows", type=int, default=0)
     p.add_argument("--caqr-arity", type=int, default=0, help="0 = the library default")
@@ -176,8 +176,11 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------- ours --
-def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False):
-    m, n = args.m, args.n
+def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False, flags=0, m=None, n=None):
+    """tsqr_refactor + tsqr_form_q per step on an m x n N(0, 1) matrix.  The timed
+    steps run without the library's stage events; with timing=True a second pass
+    of the same steps records them (per-stage device times for the roofline)."""
+    m, n = m or args.m, n or args.n
     dev = torch.device("cuda")
     from paper_0808_2664_gb300 import inputs
 
@@ -185,7 +188,7 @@ def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False):
     A = tq.colmajor(m, n, dtype, dev)
     Q = tq.colmajor(m, n, dtype, dev)
     R = tq.colmajor(n, n, dtype, dev)
-    q = tq.tsqr_q_create(m, n, dtype, dev, leaf_rows=args.leaf_rows, arity=args.arity)
+    q = tq.tsqr_q_create(m, n, dtype, dev, leaf_rows=args.leaf_rows, arity=args.arity, flags=flags)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -196,8 +199,6 @@ def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False):
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    if timing:
-        q.set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
@@ -205,8 +206,21 @@ def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_total = e0.elapsed_time(e1)
-    stages = q.stage_times() if timing else None
+    # The restore copy of A, timed alone, so that the kernels' share is known.
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(steps):
+        A.copy_(A0)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    copy_ms = c0.elapsed_time(c1) / steps
+    stages = None
     if timing:
+        q.set_timing(True)
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        stages = q.stage_times()
         q.set_timing(False)
     status = q.sync_status()
     # Backward error and orthogonality of the last step, in FP64 on the device.
@@ -216,7 +230,7 @@ def run_variant(tq, torch, args, dtype, steps, warmup, seed, timing=False):
     info = q.info()
     del A64, Q64, R64
     return {"ms_total": ms_total, "stages": stages, "status": status, "berr": berr, "orth": orth, "info": info,
-            "q": q, "A0": A0, "A": A, "Q": Q, "R": R}
+            "q": q, "A0": A0, "A": A, "Q": Q, "R": R, "copy_ms": copy_ms}
 
 
 def caqr_run(tq, torch, args, steps, warmup, dtype=None, upd=None):
@@ -292,7 +306,12 @@ def caqr_run(tq, torch, args, steps, warmup, dtype=None, upd=None):
     return {"value": flops / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "n": n, "b": b,
             "storage": str(dtype).replace("torch.", ""),
             "update_precision": {tq.PREC_FP64: "fp64", tq.PREC_FP32: "fp32", tq.UPDATE_BF16X3: "3xbf16"}[upd],
-            "backward_error": berr, "orthogonality": orth, "tolerance": 10 * n * eps * n ** 0.5,
+            "backward_error": berr, "orthogonality": orth,
+            # FP64: 10 n eps sqrt(m); FP32 storage: c sqrt(n) eps with c = 2 (FP32 products) or
+            # 1 (3xBF16 products), orthogonality n eps32 (the tests' bounds).
+            "tolerance": (10 * n * eps * n ** 0.5 if upd == tq.PREC_FP64 else
+                          (2.0 if upd == tq.PREC_FP32 else 1.0) * n ** 0.5 * eps),
+            "orthogonality_tolerance": 10 * n * eps * n ** 0.5 if upd == tq.PREC_FP64 else n * 2.0 ** -23,
             "status": q.sync_status(), "update_roofline": roof,
             "stage_ms_per_step": {k: v[0] / steps for k, v in st.items()}}
 
@@ -411,6 +430,48 @@ def grad_run(tq, torch, dtype, steps, warmup, m=1 << 20, n=128):
     return res
 
 
+def lstsq_run(tq, torch, args, steps, warmup, k=16):
+    """Least squares (Section 1) for k right-hand sides: tsqr_refactor + tsqr_lstsq per step
+    (leaves, tree, Q^T B through the tree, back substitution, residual norms)."""
+    m, n = args.m, args.n
+    from paper_0808_2664_gb300 import inputs
+
+    dev = torch.device("cuda")
+    A0 = inputs.gaussian_device(m, n, 6100).t()
+    B0 = inputs.gaussian_device(m, k, 6101).t()
+    A, B = tq.colmajor(m, n, torch.float64, dev), tq.colmajor(m, k, torch.float64, dev)
+    X = tq.colmajor(n, k, torch.float64, dev)
+    R = tq.colmajor(n, n, torch.float64, dev)
+    q = tq.tsqr_q_create(m, n, torch.float64, dev)
+
+    def step():
+        A.copy_(A0)
+        B.copy_(B0)
+        q.refactor(A, R)
+        return q.lstsq(R, B, X)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        _, rn = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # Optimality check on the device: the residual is orthogonal to range(A).
+    Ad, Bd = A0.double(), B0.double()
+    res = Ad @ X - Bd
+    ortho = (torch.linalg.norm(Ad.t() @ res) / (torch.linalg.norm(Ad) * torch.linalg.norm(res))).item()
+    rn_err = (torch.linalg.norm(torch.linalg.norm(res, dim=0) - rn) / torch.linalg.norm(rn)).item()
+    status = q.sync_status()
+    q.destroy()
+    return {"value": m / (ms / 1e3), "unit": "rows/s", "ms_per_step": ms, "k": k,
+            "normal_equations_residual": ortho, "residual_norm_rel_err": rn_err,
+            "tolerance": 10 * n * 2.0 ** -52 * m ** 0.5, "status": status}
+
+
 def measured_hbm():
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -450,8 +511,65 @@ def e2e_run(tq, torch, args, q, steps, warmup):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     es = 8
+    # Plain pinned copies of the same buffers, each alone: the end-to-end step cannot beat
+    # max(H2D, device work) + max(D2H, form) when the copies overlap only their own phase.
+    def copy_gbs(fn):
+        fn()
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(3):
+            fn()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        return 3 * m * n * es / (c0.elapsed_time(c1) / 1e3) / 1e9
+
+    h2d = copy_gbs(lambda: A.copy_(Ah, non_blocking=True))
+    d2h = copy_gbs(lambda: Qh.copy_(Q, non_blocking=True))
     return {"value": m * steps / (ms / 1e3), "unit": "rows/s", "h2d_bytes_per_step": m * n * es,
-            "d2h_bytes_per_step": m * n * es + n * n * es}
+            "d2h_bytes_per_step": m * n * es + n * n * es, "ms_per_step": ms / steps,
+            "pinned_h2d_gbs": h2d, "pinned_d2h_gbs": d2h, "host_cpus": sorted(os.sched_getaffinity(0))[:1] +
+            sorted(os.sched_getaffinity(0))[-1:], "gpu_numa_node": _gpu_numa_node(torch)}
+
+
+def _gpu_numa_node(torch):
+    """NUMA node of the current GPU from sysfs (None if unknown)."""
+    try:
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        bus = f"{int(p.pci_domain_id):04x}:{int(p.pci_bus_id):02x}:{int(p.pci_device_id):02x}.0"
+    except Exception:
+        return None
+    for cand in (bus,):
+        path = f"/sys/bus/pci/devices/{cand}/numa_node"
+        if os.path.exists(path):
+            try:
+                v = int(open(path).read().strip())
+                return v if v >= 0 else None
+            except (OSError, ValueError):
+                return None
+    return None
+
+
+def _bind_to_gpu_node(torch):
+    """Run on the host cores of the GPU's NUMA node, so that pinned buffers are allocated
+    there and host-device copies do not cross sockets (no-op when the node is unknown)."""
+    node = _gpu_numa_node(torch)
+    if node is None:
+        return
+    try:
+        spec = open(f"/sys/devices/system/node/node{node}/cpulist").read().strip()
+    except OSError:
+        return
+    cpus = set()
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    cpus &= os.sched_getaffinity(0)
+    if cpus:
+        os.sched_setaffinity(0, cpus)
 
 
 def ours(args, world, rank, local):
@@ -513,6 +631,7 @@ def ours(args, world, rank, local):
 
     e2e = None
     if not args.no_e2e:
+        _bind_to_gpu_node(torch)
         e2e = e2e_run(tq, torch, args, r["q"], steps=max(3, args.steps // 2), warmup=2)
         e2e["value"] *= world
 
@@ -521,12 +640,47 @@ def ours(args, world, rank, local):
     del r["A0"], r["A"], r["Q"]
     torch.cuda.empty_cache()
     if "mixed" in want:
-        v = run_variant(tq, torch, args, torch.float32, max(3, args.steps), 3, seed=3000 + rank)
+        ks = max(3, args.steps)
+        v = run_variant(tq, torch, args, torch.float32, ks, 3, seed=3000 + rank, timing=True)
+        lf_ms = v["stages"]["leaf_factor"][0] / max(1, v["stages"]["leaf_factor"][1])
+        la_ms = v["stages"]["leaf_apply"][0] / max(1, v["stages"]["leaf_apply"][1])
+        hbm = measured_hbm()
+        # Leaf factor: reads A and writes Y (2 m n 4 bytes per launch); form: reads Y's slots and
+        # Y, writes Q (2 m n 4 bytes).
+        lf_gbs = 2.0 * m * n * 4 / (lf_ms / 1e3) / 1e9
         variants["mixed_fp32_storage_fp64_reflectors"] = {
-            "value": world * m / (v["ms_total"] / max(3, args.steps) / 1e3), "unit": "rows/s",
-            "ms_per_step": v["ms_total"] / max(3, args.steps), "backward_error": v["berr"],
-            "orthogonality": v["orth"], "status": v["status"]}
+            "value": world * m / (v["ms_total"] / ks / 1e3), "unit": "rows/s",
+            "ms_per_step": v["ms_total"] / ks, "restore_copy_ms": v["copy_ms"], "backward_error": v["berr"],
+            "orthogonality": v["orth"], "tolerance": 10 * n * 2.0 ** -23 * m ** 0.5, "status": v["status"],
+            "roofline": {"bound": "hbm", "kernel": "leaf_factor_kernel<float>", "achieved": lf_gbs, "peak": hbm,
+                         "unit": "GB/s", "frac": lf_gbs / hbm,
+                         "form_kernel_gbs": 2.0 * m * n * 4 / (la_ms / 1e3) / 1e9},
+            "stage_ms_per_launch": {k2: (x[0] / x[1] if x[1] else 0.0) for k2, x in v["stages"].items()}}
         del v
+        torch.cuda.empty_cache()
+    if "hybrid" in want:
+        ks = max(3, args.steps // 2)
+        v = run_variant(tq, torch, args, torch.float64, ks, 2, seed=2000 + rank, timing=True,
+                        flags=tq.FLAG_HYBRID_TREE)
+        ch = v["q"].chains()
+        variants["hybrid_tree_fp64"] = {
+            "value": world * m / (v["ms_total"] / ks / 1e3), "unit": "rows/s", "ms_per_step": v["ms_total"] / ks,
+            "chains": ch["chains"], "leaves_per_chain": ch["leaves_per_chain"], "levels": v["info"]["levels"],
+            "leaf_rows": v["info"]["leaf_rows"], "backward_error": v["berr"], "orthogonality": v["orth"],
+            "tolerance": 10 * n * 2.0 ** -52 * m ** 0.5, "status": v["status"],
+            "stage_ms_per_step": {k2: x[0] / ks for k2, x in v["stages"].items()}}
+        del v
+        torch.cuda.empty_cache()
+        mf = 65536
+        v = run_variant(tq, torch, args, torch.float64, 3, 1, seed=2100 + rank, flags=tq.FLAG_FLAT_TREE, m=mf)
+        variants["flat_tree_fp64_m65536"] = {
+            "value": world * mf / (v["ms_total"] / 3 / 1e3), "unit": "rows/s", "ms_per_step": v["ms_total"] / 3,
+            "backward_error": v["berr"], "orthogonality": v["orth"], "status": v["status"],
+            "note": "one CTA streams every leaf (sequential TSQR): a latency reference, not a throughput form"}
+        del v
+        torch.cuda.empty_cache()
+    if "lstsq" in want:
+        variants["lstsq_fp64_k16"] = lstsq_run(tq, torch, args, steps=max(3, args.steps // 2), warmup=2)
         torch.cuda.empty_cache()
     if "caqr" in want:
         variants["caqr_fp64"] = caqr_run(tq, torch, args, steps=3, warmup=3)
