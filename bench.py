@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--caqr-arity", type=int, default=0, help="0 = the library default")
     p.add_argument("--caqr-n", type=int, default=8192, help="square CAQR size for the CAQR variant")
     p.add_argument("--caqr-b", type=int, default=64)
+    p.add_argument("--batched-count", type=int, default=2048, help="matrices in the batched variant")
+    p.add_argument("--batched-autotune", type=int, default=1, help="0: default tile and arity, no autotuner")
     p.add_argument("--peaks", action="store_true",
                    help="compile and run bench_peaks.cu (FP64 / FP32 FMA and DMMA throughput probes) and exit")
     return p.parse_args()
@@ -316,7 +318,7 @@ def caqr_run(tq, torch, args, steps, warmup, dtype=None, upd=None):
             "stage_ms_per_step": {k: v[0] / steps for k, v in st.items()}}
 
 
-def batched_run(tq, torch, args, steps, warmup, count=2048):
+def batched_run(tq, torch, args, steps, warmup, count=2048, autotune=True):
     """2048 uneven FP32 matrices (m log-uniform in [1024, 65536], n in {16, 32, 64}):
     one persistent graph-replayed launch (autotuned) vs a loop over the plain path."""
     from paper_0808_2664_gb300 import inputs
@@ -333,7 +335,7 @@ def batched_run(tq, torch, args, steps, warmup, count=2048):
         As.append(buf[off:off + m * n].view(n, m).t())
         off += m * n
     buf.copy_(buf0)
-    b = tq.Batch(As, autotune=True)
+    b = tq.Batch(As, autotune=autotune)
     info = b.info()
 
     def timed(run, k, w):
@@ -532,6 +534,65 @@ def e2e_run(tq, torch, args, q, steps, warmup):
             sorted(os.sched_getaffinity(0))[-1:], "gpu_numa_node": _gpu_numa_node(torch)}
 
 
+def dist_run(tq, torch, dist, args, rank, world):
+    """Row-slab TSQR across the ranks (Section 2.1 parallel TSQR): each rank holds an m x n slab;
+    one step = restore the slab, local TSQR, all_gather of the packed R triangles, the stacked
+    triangles' structured QR, and this rank's block of the thin Q.  Timed between barriers with a
+    device synchronize on both sides; the max over ranks.  The end-to-end form adds the pinned
+    H2D copy of the slab and the D2H copies of Q_local and R to every step."""
+    from paper_0808_2664_gb300 import distributed as D
+    from paper_0808_2664_gb300 import inputs
+
+    m, n = args.m, args.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A0 = inputs.gaussian_device(m, n, 2200 + rank).t()
+    A = tq.colmajor(m, n, torch.float64, dev)
+    Q = tq.colmajor(m, n, torch.float64, dev)
+    dt = D.DistTsqr(m, n, torch.float64, dev)
+
+    def timed(step, k, w):
+        for _ in range(w):
+            step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t = torch.tensor([e0.elapsed_time(e1) / k], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return t.item()
+
+    def step():
+        A.copy_(A0)
+        dt.factor(A, Q)
+
+    ms = timed(step, args.steps, args.warmup)
+    Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    Ah.copy_(A0)
+    Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+
+    def step_host():
+        A.copy_(Ah, non_blocking=True)
+        _, R = dt.factor(A, Q)
+        Qh.copy_(Q, non_blocking=True)
+        Rh.copy_(R, non_blocking=True)
+
+    ms_e2e = timed(step_host, max(3, args.steps // 2), 2)
+    # Accuracy of the distributed factors on this rank's slab: A_p = Q_p R.
+    A64 = A0.double()
+    berr = (torch.linalg.norm(A64 - Q @ dt.R) / torch.linalg.norm(A64)).item()
+    dt.destroy()
+    return {"ms_per_step": ms, "slab_backward_error": berr,
+            "e2e": {"value": world * m / (ms_e2e / 1e3), "unit": "rows/s", "h2d_bytes_per_step": m * n * 8,
+                    "d2h_bytes_per_step": m * n * 8 + n * n * 8}}
+
+
 def _gpu_numa_node(torch):
     """NUMA node of the current GPU from sysfs (None if unknown)."""
     try:
@@ -585,7 +646,7 @@ def ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:
         rate, ms, dt, cores = oracle_rows_per_s(args.m, args.n, args.cpu_seconds)
         cpu = {"value": rate, "unit": "rows/s", "cores": cores, "kind": "oracle",
                "sample": f"{ms} x {args.n} rows (factor + thin Q) of the {args.m} x {args.n} workload, {dt:.1f} s"}
@@ -594,13 +655,14 @@ def ours(args, world, rank, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    dres = None
     with ClockSampler(local) as clk:
         r = run_variant(tq, torch, args, torch.float64, args.steps, args.warmup, seed=2000 + rank, timing=True)
+        if dist:
+            dres = dist_run(tq, torch, dist, args, rank, world)
     ms_step = r["ms_total"] / args.steps
     if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = t.item()
+        ms_step = dres["ms_per_step"]  # row-slab TSQR across the ranks, max over ranks
     m, n = args.m, args.n
     value = world * m / (ms_step / 1e3)
 
@@ -630,13 +692,16 @@ def ours(args, world, rank, local):
     launches = int(sum(v[1] for v in st.values()))
 
     e2e = None
-    if not args.no_e2e:
+    if dist:
+        e2e = dres["e2e"]
+    elif not args.no_e2e:
         _bind_to_gpu_node(torch)
         e2e = e2e_run(tq, torch, args, r["q"], steps=max(3, args.steps // 2), warmup=2)
         e2e["value"] *= world
 
     variants = {}
-    want = set() if args.no_variants else set(args.variants.split(","))
+    # At N > 1 the line measures the row-slab exchange; the single-GPU variants run at N = 1.
+    want = set() if (args.no_variants or world > 1) else set(args.variants.split(","))
     del r["A0"], r["A"], r["Q"]
     torch.cuda.empty_cache()
     if "mixed" in want:
@@ -691,7 +756,8 @@ def ours(args, world, rank, local):
         variants["caqr_3xbf16_update"] = caqr_run(tq, torch, args, 3, 3, torch.float32, tq.UPDATE_BF16X3)
         torch.cuda.empty_cache()
     if "batched" in want:
-        variants["batched_fp32_2048"] = batched_run(tq, torch, args, steps=5, warmup=3)
+        variants[f"batched_fp32_{args.batched_count}"] = batched_run(
+            tq, torch, args, steps=5, warmup=3, count=args.batched_count, autotune=bool(args.batched_autotune))
         torch.cuda.empty_cache()
     if "grad" in want:
         variants["grad_fp64_1Mx128"] = grad_run(tq, torch, torch.float64, steps=3, warmup=3)
@@ -702,7 +768,10 @@ def ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(args), leaves=nl, levels=info["levels"], leaf_rows=h, arity=info["arity"]),
+            "config": dict(workload_config(args), leaves=nl, levels=info["levels"], leaf_rows=h, arity=info["arity"],
+                           parallelism=(f"{world} row slabs of {m} rows, one all_gather of packed R, structured "
+                                        "top factorisation on every rank" if world > 1 else "1 GPU")),
+            "single_gpu_ms_per_step": r["ms_total"] / args.steps,
             "backward_error": r["berr"], "orthogonality": r["orth"],
             "tolerance": 10 * n * 2.0 ** -52 * m ** 0.5, "device_status": r["status"],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

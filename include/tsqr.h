@@ -148,6 +148,15 @@ int tsqr_apply_q(tsqr_q_t q, int64_t k, void* C, int64_t ldc, tsqr_stream_t stre
 int tsqr_form_q(tsqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream);
 
 /*
+ * tsqr_form_q_mul: Q_thin X (m x k, device, ldq >= m) for X (n x k, device,
+ * ldx >= n), formed like tsqr_form_q from [X; 0] instead of [I_n; 0]: the
+ * rank-local block of the thin Q in parallel TSQR (Section 2.1), where X is
+ * that rank's n-row block of the Q of the stacked R factors.  The signs D are
+ * included (Q_thin X = Q_tree [D X; 0]).  Q must not alias A or X.
+ */
+int tsqr_form_q_mul(tsqr_q_t q, int64_t k, const void* X, int64_t ldx, void* Q, int64_t ldq, tsqr_stream_t stream);
+
+/*
  * tsqr_factor_form_host: A = QR of a HOST matrix, with thin Q and R written
  * back to HOST memory (Section 2.1: factor, then the Q factor with n
  * columns), for data that lives on the host.  One call = tsqr_refactor +

@@ -150,6 +150,17 @@ class QTree:
         check(lib().tsqr_form_q(self.ptr, ctypes.c_void_p(Q.data_ptr()), ldq, _stream(Q)), "tsqr_form_q")
         return Q
 
+    def form_q_mul(self, X, Q=None):
+        """Q_thin X (m x k) for the n x k column-major CUDA matrix X (tsqr_form_q_mul)."""
+        if X.dtype != self.dtype or X.shape[0] != self.n:
+            raise ValueError(f"X must be {self.n} x k of dtype {self.dtype}")
+        k = X.shape[1]
+        if Q is None:
+            Q = colmajor(self.m, k, self.dtype, X.device)
+        check(lib().tsqr_form_q_mul(self.ptr, k, ctypes.c_void_p(X.data_ptr()), _ld(X, "X"),
+                                    ctypes.c_void_p(Q.data_ptr()), _ld(Q, "Q"), _stream(Q)), "tsqr_form_q_mul")
+        return Q
+
     def factor_form_host(self, A_host, Q_host, R_host, A, Q, R):
         """QR of a host matrix with Q and R written back to host memory, the copies pipelined
         with the leaf work (tsqr_factor_form_host).  A_host, Q_host, R_host: column-major CPU

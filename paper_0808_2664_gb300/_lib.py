@@ -37,6 +37,7 @@ SIGNATURES = {
     "tsqr_apply_qt": ([vp, i64, vp, i64, vp], ctypes.c_int),
     "tsqr_apply_q": ([vp, i64, vp, i64, vp], ctypes.c_int),
     "tsqr_form_q": ([vp, vp, i64, vp], ctypes.c_int),
+    "tsqr_form_q_mul": ([vp, i64, vp, i64, vp, i64, vp], ctypes.c_int),
     "tsqr_factor_form_host": ([vp, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp], ctypes.c_int),
     "tsqr_sync_status": ([vp, vp], ctypes.c_int),
     "tsqr_q_info": ([vp, pi64, pi64, pi32, pi64, pi64, pi32, pi32], ctypes.c_int),

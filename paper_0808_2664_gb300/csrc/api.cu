@@ -411,10 +411,12 @@ LeafApplyArgs<T> leaf_apply_args(const tsqr_q_s* q, int64_t k, T* C, int64_t ldc
 // Tree stage of forming the thin Q: the root slot starts as diag(d), every
 // other row is produced top-down without being read.
 template <typename T>
-cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s);
+cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s, int64_t k = -1, const T* X = nullptr,
+                          int64_t ldx = 0);
 
 template <typename T>
-cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc, cudaStream_t s) {
+cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc, cudaStream_t s, const T* X = nullptr,
+                      int64_t ldx = 0) {
   cudaError_t e = cudaSuccess;
   LeafApplyArgs<T> la = leaf_apply_args(q, k, C, ldc, 0, q->nleaves);
   auto node = [&](int l, int md) {
@@ -471,15 +473,19 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
     }
     return leaf(kApplyQ);
   }
-  if ((e = run_tree_form(q, C, ldc, s)) != cudaSuccess) return e;
+  if ((e = run_tree_form(q, C, ldc, s, k, X, ldx)) != cudaSuccess) return e;
   return leaf(kApplyForm);
 }
 
+// Forms Q [X; 0] (X n x k) when X is given, the thin Q (X = I, k = n) otherwise.
 template <typename T>
-cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s) {
+cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s, int64_t k, const T* X, int64_t ldx) {
   cudaError_t e = cudaSuccess;
+  if (k < 0) k = q->n;
   StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
-  if ((e = launch_init_form(C, ldc, (int)q->n, (const T*)q->d, s)) != cudaSuccess) return e;
+  e = X ? launch_init_form_mul(C, ldc, (int)q->n, k, (const T*)q->d, X, ldx, s)
+        : launch_init_form(C, ldc, (int)q->n, (const T*)q->d, s);
+  if (e != cudaSuccess) return e;
   for (int l = q->levels; l >= 1; --l) {
     NodeApplyArgs<T> na{};
     na.Y = (const T*)q->nodeY[l - 1];
@@ -491,7 +497,7 @@ cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s) 
     na.slot_stride = slot_stride(q, l);
     na.C = C;
     na.ldc = ldc;
-    na.k = q->n;
+    na.k = k;
     na.mode = kApplyForm;
     if ((e = launch_node_apply(na, s)) != cudaSuccess) return e;
   }
@@ -730,6 +736,21 @@ int tsqr_form_q(tsqr_q_t q, void* Q, int64_t ldq, tsqr_stream_t stream) {
   if (Q == q->A) return -2;
   cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, kApplyForm, q->n, (double*)Q, ldq, (cudaStream_t)stream)
                                             : run_apply<float>(q, kApplyForm, q->n, (float*)Q, ldq, (cudaStream_t)stream);
+  return cuda_err(e);
+}
+
+int tsqr_form_q_mul(tsqr_q_t q, int64_t k, const void* X, int64_t ldx, void* Q, int64_t ldq, tsqr_stream_t stream) {
+  if (!valid(q) || !q->factored) return TSQR_ERR_HANDLE;
+  if (k < 0) return -2;
+  if (k == 0) return TSQR_OK;
+  if (!X) return -3;
+  if (ldx < q->n) return -4;
+  if (!Q || Q == q->A) return -5;
+  if (ldq < q->m) return -6;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = q->prec == TSQR_PREC_FP64
+                      ? run_apply<double>(q, kApplyForm, k, (double*)Q, ldq, s, (const double*)X, ldx)
+                      : run_apply<float>(q, kApplyForm, k, (float*)Q, ldq, s, (const float*)X, ldx);
   return cuda_err(e);
 }
 

@@ -398,6 +398,18 @@ __global__ void init_form_kernel(T* Q, int64_t ldq, int n, const T* d) {
   }
 }
 
+// Q(0:n, 0:k) = diag(d) X (X n x k, ld ldx): the slot rows that start forming Q X.
+template <typename T>
+__global__ void init_form_mul_kernel(T* Q, int64_t ldq, int n, int64_t k, const T* d, const T* X, int64_t ldx) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * k;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % n);
+    const int64_t c = idx / n;
+    const T x = X[i + c * ldx];
+    Q[i + c * ldq] = d ? d[i] * x : x;
+  }
+}
+
 template <typename T>
 __global__ void copy_upper_kernel(const T* src, int n, T* dst, int64_t ldd) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
@@ -505,6 +517,13 @@ cudaError_t launch_scale_rows(T* C, int64_t ldc, int n, int64_t k, const T* d, c
 }
 
 template <typename T>
+cudaError_t launch_init_form_mul(T* Q, int64_t ldq, int n, int64_t k, const T* d, const T* X, int64_t ldx,
+                                 cudaStream_t s) {
+  init_form_mul_kernel<T><<<small_grid((int64_t)n * k), 256, 0, s>>>(Q, ldq, n, k, d, X, ldx);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_init_form(T* Q, int64_t ldq, int n, const T* d, cudaStream_t s) {
   init_form_kernel<T><<<small_grid((int64_t)n * n), 256, 0, s>>>(Q, ldq, n, d);
   return cudaGetLastError();
@@ -522,6 +541,7 @@ cudaError_t launch_copy_upper(const T* src, int n, T* dst, int64_t ldd, cudaStre
   template cudaError_t launch_sign_fix<T>(const T*, int, T*, T*, int64_t, bool, cudaStream_t);       \
   template cudaError_t launch_scale_rows<T>(T*, int64_t, int, int64_t, const T*, cudaStream_t);      \
   template cudaError_t launch_init_form<T>(T*, int64_t, int, const T*, cudaStream_t);                \
+  template cudaError_t launch_init_form_mul<T>(T*, int64_t, int, int64_t, const T*, const T*, int64_t, cudaStream_t); \
   template cudaError_t launch_copy_upper<T>(const T*, int, T*, int64_t, cudaStream_t);
 TSQR_INSTANTIATE(double)
 TSQR_INSTANTIATE(float)

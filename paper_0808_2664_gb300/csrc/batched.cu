@@ -452,7 +452,9 @@ int autotune(int32_t count, const int64_t* m, const int64_t* n, int32_t prec, in
     else
       fill_uniform_kernel<float><<<1024, 256, 0, s>>>((float*)scratch, elems, 12345);
   };
-  const int kbs64[] = {34, 68, 136}, kbs32[] = {68, 136, 200};
+  // Smaller tiles let more leaf CTAs share an SM (the leaf column loop is
+  // latency-bound); larger ones make shorter trees.
+  const int kbs64[] = {24, 34, 68, 136}, kbs32[] = {34, 48, 68, 136};
   const int qs[] = {2, 4, 8};
   float best = 1e30f;
   *best_kb = default_tile_kb(es);
@@ -460,7 +462,7 @@ int autotune(int32_t count, const int64_t* m, const int64_t* n, int32_t prec, in
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int ki = 0; ki < 3; ++ki) {
+  for (int ki = 0; ki < 4; ++ki) {
     for (int qi = 0; qi < 3; ++qi) {
       const int kb = es == 8 ? kbs64[ki] : kbs32[ki];
       tsqr_batch_s* b = nullptr;

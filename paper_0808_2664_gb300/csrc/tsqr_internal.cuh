@@ -169,6 +169,10 @@ cudaError_t launch_scale_rows(T* C, int64_t ldc, int n, int64_t k, const T* d, c
 // Q(0:n, 0:n) = diag(d) (the identity when d is null).
 template <typename T>
 cudaError_t launch_init_form(T* Q, int64_t ldq, int n, const T* d, cudaStream_t s);
+// Q(0:n, 0:k) = diag(d) X (d may be null).
+template <typename T>
+cudaError_t launch_init_form_mul(T* Q, int64_t ldq, int n, int64_t k, const T* d, const T* X, int64_t ldx,
+                                 cudaStream_t s);
 // Copy the n x n upper triangle of src (ld n) into dst (ldd), zero below.
 template <typename T>
 cudaError_t launch_copy_upper(const T* src, int n, T* dst, int64_t ldd, cudaStream_t s);

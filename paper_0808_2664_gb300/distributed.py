@@ -10,7 +10,9 @@ whole matrix is block-row distributed: rank p holds Q_p * Qtop[p*n:(p+1)*n, :],
 formed by applying the local Q-tree to [Qtop block; 0].
 
 The local factorisation is pluggable: by default the CUDA TSQR of this
-package (one GPU per rank, NCCL); tests pass a CPU stand-in and use gloo.
+package (one GPU per rank, NCCL) with the stacked triangles factored by the
+structured tree-node kernel; tests pass a CPU stand-in and use gloo.
+DistTsqr is the plan-once form (handles and buffers kept across calls).
 """
 from __future__ import annotations
 
@@ -43,7 +45,7 @@ def unpack_upper(v: torch.Tensor, n: int) -> torch.Tensor:
 
 
 def gpu_local_qr(A: torch.Tensor):
-    """Local TSQR (CAQR for FP64 n > 64) on this rank's GPU; apply_q uses the kept Q-tree."""
+    """Local TSQR (CAQR for FP64 n > 64) on this rank's GPU; apply_q(X) = Q_thin X from the kept Q-tree."""
     from . import as_colmajor, caqr_factor, colmajor, tsqr_factor
 
     m, n = A.shape
@@ -52,25 +54,57 @@ def gpu_local_qr(A: torch.Tensor):
     if A.dtype == torch.float64 and n > 64:
         q = caqr_factor(W, b=64)
         R = as_colmajor(torch.triu(W[:n, :n]))
-    else:
-        R, q = tsqr_factor(W)
+
+        def apply_q(X: torch.Tensor) -> torch.Tensor:
+            E = colmajor(m, X.shape[1], A.dtype, A.device)
+            E.zero_()
+            E[:n, :] = X
+            return q.apply_q(E)
+
+        return R, apply_q
+    R, q = tsqr_factor(W)
 
     def apply_q(X: torch.Tensor) -> torch.Tensor:
-        E = colmajor(m, X.shape[1], A.dtype, A.device)
-        E.zero_()
-        E[:n, :] = X
-        return q.apply_q(E)
+        return q.form_q_mul(as_colmajor(X.contiguous()))
 
     return R, apply_q
 
 
-def dist_tsqr(A_local: torch.Tensor, group=None, local_qr: Optional[LocalQR] = None, want_q: bool = True):
+def gpu_stack_qr(stack: torch.Tensor):
+    """QR of P stacked n x n upper triangles (P n x n) on the GPU: leaves of n rows
+    (each already triangular) and one structured tree node of arity P (P <= 16) or a
+    4-ary tree above them, so the triangles' zeros are never touched (Section 2.1)."""
+    from . import as_colmajor, tsqr_factor
+
+    pn, n = stack.shape
+    P = pn // n
+    W = as_colmajor(stack.detach().clone())
+    W = as_colmajor(W)
+    if W.dtype == torch.float64 and n > 64:
+        return gpu_local_qr(stack)
+    arity = P if 2 <= P <= 16 else 4
+    R, q = tsqr_factor(W, leaf_rows=n, arity=arity)
+
+    def apply_q(X: torch.Tensor) -> torch.Tensor:
+        return q.form_q_mul(as_colmajor(X.contiguous()))
+
+    return R, apply_q
+
+
+def dist_tsqr(A_local: torch.Tensor, group=None, local_qr: Optional[LocalQR] = None, want_q: bool = True,
+              top_qr: Optional[LocalQR] = None):
     """TSQR of the row-distributed matrix [A_0; ...; A_{P-1}] (A_p on rank p, m_p x n, m_p >= n).
 
     Returns (Q_local, R): R (n x n, diag >= 0) is identical on every rank and
     Q_local is this rank's m_p x n block of the thin Q (None if not wanted).
+    The top of the tree factors the gathered triangles with top_qr (default:
+    the structured GPU node kernel when local_qr is the GPU path, local_qr
+    otherwise).
     """
-    local_qr = local_qr or gpu_local_qr
+    if local_qr is None:
+        local_qr = gpu_local_qr
+        top_qr = top_qr or gpu_stack_qr
+    top_qr = top_qr or local_qr
     world = dist.get_world_size(group)
     rank = dist.get_rank(group)
     n = A_local.shape[1]
@@ -79,7 +113,7 @@ def dist_tsqr(A_local: torch.Tensor, group=None, local_qr: Optional[LocalQR] = N
     gathered = [torch.empty_like(packed) for _ in range(world)]
     dist.all_gather(gathered, packed, group=group)
     stack = torch.cat([unpack_upper(v, n) for v in gathered], dim=0)  # P*n x n, stacked triangles
-    R, apply_top = local_qr(stack)
+    R, apply_top = top_qr(stack)
     if not want_q:
         return None, R
     eye = torch.zeros((n, n), dtype=stack.dtype, device=stack.device)
@@ -87,3 +121,54 @@ def dist_tsqr(A_local: torch.Tensor, group=None, local_qr: Optional[LocalQR] = N
     Q_top = apply_top(eye)                 # thin Q of the stack, P*n x n
     block = Q_top[rank * n:(rank + 1) * n, :]
     return apply_p(block), R
+
+
+class DistTsqr:
+    """Plan-once parallel TSQR over the ranks of `group` (Section 2.1): each rank
+    factors its m_local x n slab with its own Q-tree handle, the packed R
+    triangles travel in one all_gather, every rank factors the P stacked
+    triangles with the structured tree-node kernel, and each rank forms its
+    block of the thin Q as Q_p [Qtop_p; 0].  Handles and buffers are created
+    once; factor() allocates nothing on the device but the outputs it is not
+    given."""
+
+    def __init__(self, m_local: int, n: int, dtype=torch.float64, device=None, group=None):
+        from . import colmajor, tsqr_q_create
+
+        self.group = group
+        self.world = dist.get_world_size(group)
+        self.rank = dist.get_rank(group)
+        self.m, self.n, self.dtype = m_local, n, dtype
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        P = self.world
+        self.local = tsqr_q_create(m_local, n, dtype, self.device)
+        self.top = tsqr_q_create(P * n, n, dtype, self.device, leaf_rows=n, arity=P if 2 <= P <= 16 else 4)
+        self.R_local = colmajor(n, n, dtype, self.device)
+        self.R = colmajor(n, n, dtype, self.device)
+        self.stack = colmajor(P * n, n, dtype, self.device)
+        npk = n * (n + 1) // 2
+        self.gathered = [torch.empty(npk, dtype=dtype, device=self.device) for _ in range(P)]
+        self.Qtop = colmajor(P * n, n, dtype, self.device)
+        self.iu = _upper_index(n, self.device)
+
+    def factor(self, A_local: torch.Tensor, Q_local: Optional[torch.Tensor] = None):
+        """(Q_local, R) of the distributed matrix; A_local is overwritten by its reflectors."""
+        from . import as_colmajor
+
+        n = self.n
+        self.local.refactor(A_local, self.R_local)
+        packed = self.R_local[self.iu[0], self.iu[1]].contiguous()
+        dist.all_gather(self.gathered, packed, group=self.group)
+        self.stack.zero_()
+        for p, v in enumerate(self.gathered):
+            blk = self.stack[p * n:(p + 1) * n]
+            blk[self.iu[0], self.iu[1]] = v
+        self.top.refactor(self.stack, self.R)
+        self.top.form_q(self.Qtop)
+        X = as_colmajor(self.Qtop[self.rank * n:(self.rank + 1) * n].contiguous())
+        Q_local = self.local.form_q_mul(X, Q_local)
+        return Q_local, self.R
+
+    def destroy(self):
+        self.local.destroy()
+        self.top.destroy()
