@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-variants", action="store_true")
-    p.add_argument("--variants", default="mixed,hybrid,lstsq,caqr,caqr_mixed,batched,grad",
+    p.add_argument("--variants", default="mixed,hybrid,rec,lstsq,caqr,caqr_mixed,batched,grad",
                    help="comma list of extra measurements")
     p.add_argument("--caqr-leaf-rows", type=int, default=0)
     p.add_argument("--caqr-arity", type=int, default=0, help="0 = the library default")
@@ -744,6 +744,17 @@ def ours(args, world, rank, local):
             "note": "one CTA streams every leaf (sequential TSQR): a latency reference, not a throughput form"}
         del v
         torch.cuda.empty_cache()
+    if "rec" in want:
+        for dt, name in ((torch.float64, "recursive_leaf_fp64"), (torch.float32, "recursive_leaf_fp32")):
+            ks = max(3, args.steps // 2)
+            v = run_variant(tq, torch, args, dt, ks, 2, seed=2300 + rank, timing=True, flags=tq.FLAG_RECURSIVE_LEAF)
+            variants[name] = {
+                "value": world * m / (v["ms_total"] / ks / 1e3), "unit": "rows/s", "ms_per_step": v["ms_total"] / ks,
+                "leaf_rows": v["info"]["leaf_rows"], "levels": v["info"]["levels"], "backward_error": v["berr"],
+                "orthogonality": v["orth"], "status": v["status"],
+                "stage_ms_per_launch": {k2: (x[0] / x[1] if x[1] else 0.0) for k2, x in v["stages"].items()}}
+            del v
+            torch.cuda.empty_cache()
     if "lstsq" in want:
         variants["lstsq_fp64_k16"] = lstsq_run(tq, torch, args, steps=max(3, args.steps // 2), warmup=2)
         torch.cuda.empty_cache()

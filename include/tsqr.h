@@ -85,7 +85,14 @@ enum tsqr_flags {
   TSQR_FLAG_HYBRID_TREE = 2,
   /* Flat tree (Section 2.1's sequential TSQR, Eq. TSQR_seq_runtime): one
      chain over all leaves, one CTA streams the whole matrix. */
-  TSQR_FLAG_FLAT_TREE = 4
+  TSQR_FLAG_FLAT_TREE = 4,
+  /* Recursive leaf QR (Elmroth and Gustavson's RGEQR3, named in Sections
+     2.1 and 3.3 for the local QR): each leaf factors its left half of
+     columns recursively, updates the right half with the left half's
+     I - Y T Y^T, factors the right half, and merges the two T factors; one
+     column is the base case.  Same outputs as the default leaf.  n <= 64;
+     not with the hybrid or flat tree. */
+  TSQR_FLAG_RECURSIVE_LEAF = 8
 };
 
 /* Tuning knobs; a zero field means "choose automatically". */

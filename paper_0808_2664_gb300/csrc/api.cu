@@ -15,6 +15,9 @@
 
 namespace tsqr {
 size_t node_factor_smem(int n, int q, size_t elem);
+size_t leaf_rec_smem(int n, int ld, size_t elem);
+template <typename T>
+cudaError_t launch_leaf_factor_rec(const LeafFactorArgs<T>& a, cudaStream_t s);
 size_t leaf_apply_smem(int n, size_t elem);
 size_t node_apply_smem(int n, int q, size_t elem);
 }  // namespace tsqr
@@ -54,6 +57,7 @@ struct tsqr_q_s {
   // Hybrid / flat tree: chains of L consecutive leaves, each a flat tree in
   // one CTA; the q-ary tree runs over the nchains chain R factors.
   bool hybrid = false;
+  bool rec = false;  // recursive (RGEQR3) leaf QR
   int64_t L = 1, nchains = 0;
   int ld_s = 0;  // shared-memory leading dimension of the leaf (or stacked) tile
   // Device workspace (owned unless external).
@@ -160,9 +164,17 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? TSQR_OK : (e == cudaErro
 // fewer than n rows.
 int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t* opts) {
   const int32_t flags = opts ? opts->flags : 0;
-  if (flags & ~(TSQR_FLAG_APPLY_BF16X3 | TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE)) return -4;
+  if (flags & ~(TSQR_FLAG_APPLY_BF16X3 | TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE | TSQR_FLAG_RECURSIVE_LEAF))
+    return -4;
   q->prec = prec;
   q->hybrid = (flags & (TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE)) != 0;
+  q->rec = (flags & TSQR_FLAG_RECURSIVE_LEAF) != 0;
+  if (q->rec && (q->hybrid || n > 64)) return TSQR_ERR_UNSUPPORTED;
+  // Shared memory of the leaf kernel this plan launches for a tile of `rows` rows.
+  auto leaf_smem = [&](int64_t rows) -> int64_t {
+    return q->rec ? (int64_t)leaf_rec_smem((int)n, leaf_factor_ld((int)rows), q->es)
+                  : (int64_t)leaf_factor_smem((int)n, leaf_factor_ld((int)rows), q->es);
+  };
   // Rows of the stacked tile [R; A_i] beyond the leaf's own rows.
   const int64_t top = q->hybrid ? n : 0;
   q->es = prec == TSQR_PREC_FP64 ? 8 : 4;
@@ -184,6 +196,7 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     h = smax / (int64_t)q->es / n / 32 * 32;
     const int64_t hcap = q->es == 8 ? 1024 : (n <= 64 ? 384 : 512);
     if (h > hcap) h = hcap;
+    while (q->rec && h - 32 >= n && leaf_smem(h) > smax) h -= 32;
     h -= top;  // hybrid: the stacked tile [R; A_i] must fit
     if (h < n) h = n;
   }
@@ -197,9 +210,7 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     if (nl > 1 && rem < n) --nl;
     q->hmax = nl > 1 ? (m - (nl - 1) * h > h ? m - (nl - 1) * h : h) : m;
     // An automatic height shrinks until a merged last leaf still fits.
-    if (!auto_h || h - 32 < n ||
-        (int64_t)leaf_factor_smem((int)n, leaf_factor_ld((int)(q->hmax + top)), q->es) <= smax)
-      break;
+    if (!auto_h || h - 32 < n || leaf_smem(q->hmax + top) <= smax) break;
     h -= 32;
   }
   q->ld_s = leaf_factor_ld((int)(q->hmax + top));
@@ -235,7 +246,7 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
     if (prec != TSQR_PREC_FP32 || n > kBf16x3MaxN || q->hybrid) return TSQR_ERR_UNSUPPORTED;
     q->upd = TSQR_UPDATE_BF16X3;
   }
-  if ((int64_t)leaf_factor_smem((int)n, (int)q->hmax + (int)top, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
+  if (leaf_smem(q->hmax + top) > smax) return TSQR_ERR_UNSUPPORTED;
   if ((int64_t)leaf_apply_smem((int)n, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
   if (q->hybrid && (int64_t)chain_apply_smem((int)n, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
   if (q->levels > 0) {
@@ -313,7 +324,7 @@ cudaError_t launch_leaf_range(tsqr_q_s* q, T* A, int64_t lda, int64_t l0, int64_
   la.tau = (T*)q->leafTau + l0 * q->n;
   la.Tw = (T*)q->leafT + l0 * nn;
   la.status = q->status;
-  return launch_leaf_factor(la, s);
+  return q->rec ? launch_leaf_factor_rec(la, s) : launch_leaf_factor(la, s);
 }
 
 template <typename T>

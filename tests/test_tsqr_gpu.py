@@ -375,3 +375,56 @@ def test_reflector_generation_accuracy(fast):
         tau, scale = Decimal(float(got[i, 1])), Decimal(float(got[i, 2]))
         ident = abs(tau * (1 + scale * scale * Decimal(float(ssq[i]))) - 2)
         assert ident <= Decimal(16 * 2.0 ** -52), (i, float(ident))
+
+
+REC_SHAPES = [(4096, 32, 256, 2), (1000, 7, 64, 2), (20000, 64, 0, 4), (300, 64, 0, 2), (2049, 1, 256, 2),
+              (777, 3, 32, 3), (513, 17, 128, 2), (65, 64, 0, 2), (9000, 33, 128, 4)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("m,n,h,q", REC_SHAPES)
+def test_recursive_leaf_matches_oracle(oracle_mod, dtype, m, n, h, q):
+    """Leaves factored by the recursive (RGEQR3) leaf QR: same R, Q and Q^T C as the oracle."""
+    A = inputs.gaussian(m, n, seed=5100 + m + n)
+    if dtype == torch.float32:
+        A = A.astype(np.float32).astype(np.float64)
+    Qo, Ro = oracle_mod.qr(A)
+    kappa = np.linalg.cond(Ro)
+    tol = tol_for(dtype, m, n)
+    Ad = dev(A, dtype)
+    R, qt = tq.tsqr_factor(Ad, leaf_rows=h, arity=q, flags=tq.FLAG_RECURSIVE_LEAF)
+    Q = qt.form_q()
+    assert qt.sync_status() == 0
+    Rh, Qh = host(R), host(Q)
+    assert np.all(np.diag(Rh) >= 0)
+    assert_colwise_close(Rh, Ro, tol * kappa, "R")
+    assert_colwise_close(Qh, Qo, tol * kappa, "Q")
+    C = inputs.gaussian(m, 9, seed=5200 + n)
+    Cd = dev(C, dtype)
+    qt.apply_qt(Cd)
+    assert_colwise_close(host(Cd)[:n], Qo.T @ C, 4 * tol * kappa, "QtC")
+    qt.destroy()
+
+
+def test_recursive_leaf_t_matches_oracle(oracle_mod):
+    """One recursive leaf: its merged T equals the oracle's larft of the same reflectors."""
+    m, n = 300, 40
+    A = inputs.gaussian(m, n, 5300)
+    f = oracle_mod.geqr2(A)
+    Ad = dev(A)
+    R, qt = tq.tsqr_factor(Ad, leaf_rows=512, flags=tq.FLAG_RECURSIVE_LEAF)
+    assert qt.info()["leaves"] == 1
+    np.testing.assert_allclose(np.tril(host(Ad), -1), np.tril(f.Y, -1), atol=100 * EPS64)
+    T = host(qt.part("T", 0, 0))
+    assert_colwise_close(T, oracle_mod.larft(f), 256 * n * EPS64, "T")
+    np.testing.assert_allclose(host(qt.part("tau", 0, 0)), f.tau, rtol=0, atol=64 * EPS64)
+    qt.destroy()
+
+
+def test_recursive_leaf_rejects_hybrid_and_wide():
+    with pytest.raises(tq.TsqrError) as ei:
+        tq.tsqr_q_create(4096, 16, torch.float64, flags=tq.FLAG_RECURSIVE_LEAF | tq.FLAG_HYBRID_TREE)
+    assert ei.value.code == 5
+    with pytest.raises(tq.TsqrError) as ei:
+        tq.tsqr_q_create(4096, 100, torch.float32, flags=tq.FLAG_RECURSIVE_LEAF)
+    assert ei.value.code == 5
