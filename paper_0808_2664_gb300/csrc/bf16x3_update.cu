@@ -219,18 +219,38 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
     const int rb = ch * kUChunk;
     unsigned char* ahi = sm + kOffA1 + (2 * buf) * kSzA1;
     unsigned char* bhi = sm + kOffB1 + (2 * buf) * kSzB1;
-    for (int idx = tid; idx < kUN * (kUChunk / 4); idx += kUThreads) {
+    // All of this thread's global loads for the chunk are issued before any
+    // of them is converted, so that their latencies overlap.
+    constexpr int kCPer = kUN * (kUChunk / 4) / kUThreads, kYPer = kUNp * (kUChunk / 4) / kUThreads;
+    float xc[kCPer][4], xy[kYPer][4];
+#pragma unroll
+    for (int t = 0; t < kCPer; ++t) {
+      const int idx = tid + t * kUThreads;
       const int quad = idx % (kUChunk / 4), c = idx / (kUChunk / 4);
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      if (c < kc) load4(Cg, a.ldc, rb + 4 * quad, c, x);
-      split_store4(ahi, ahi + kSzA1, kmaj(c, 4 * quad, kUN), x);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) xc[t][e] = 0.f;
+      if (c < kc) load4(Cg, a.ldc, rb + 4 * quad, c, xc[t]);
     }
-    for (int idx = tid; idx < kUNp * (kUChunk / 4); idx += kUThreads) {
+#pragma unroll
+    for (int t = 0; t < kYPer; ++t) {
+      const int idx = tid + t * kUThreads;
       const int quad = idx % (kUChunk / 4), p = idx / (kUChunk / 4);
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      if (p < n) load4(Yg, a.ldy, rb + 4 * quad, p, x);
-      mask_y(rb + 4 * quad, p, x);
-      split_store4(bhi, bhi + kSzB1, kmaj(p, 4 * quad, kUNp), x);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) xy[t][e] = 0.f;
+      if (p < n) load4(Yg, a.ldy, rb + 4 * quad, p, xy[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kCPer; ++t) {
+      const int idx = tid + t * kUThreads;
+      const int quad = idx % (kUChunk / 4), c = idx / (kUChunk / 4);
+      split_store4(ahi, ahi + kSzA1, kmaj(c, 4 * quad, kUN), xc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < kYPer; ++t) {
+      const int idx = tid + t * kUThreads;
+      const int quad = idx % (kUChunk / 4), p = idx / (kUChunk / 4);
+      mask_y(rb + 4 * quad, p, xy[t]);
+      split_store4(bhi, bhi + kSzB1, kmaj(p, 4 * quad, kUNp), xy[t]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   };
@@ -304,13 +324,26 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
   const int ntiles = (hl + 127) / 128;
   for (int t = 0; t < ntiles && ok; ++t) {
     const int rt = t * 128;
-    for (int idx = tid; idx < 32 * kUNp; idx += kUThreads) {
-      const int quad = idx % 32, p = idx / 32;
-      float x[4] = {0.f, 0.f, 0.f, 0.f};
-      if (p < n) load4(Yg, a.ldy, rt + 4 * quad, p, x);
-      mask_y(rt + 4 * quad, p, x);
+    {
+      constexpr int kPer = 32 * kUNp / kUThreads;
+      float xt[kPer][4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) split_store(sm + kOffA3, sm + kOffA3 + kSzA3, kmaj(4 * quad + e, p, 128), x[e]);
+      for (int t = 0; t < kPer; ++t) {
+        const int idx = tid + t * kUThreads;
+        const int quad = idx % 32, p = idx / 32;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) xt[t][e] = 0.f;
+        if (p < n) load4(Yg, a.ldy, rt + 4 * quad, p, xt[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < kPer; ++t) {
+        const int idx = tid + t * kUThreads;
+        const int quad = idx % 32, p = idx / 32;
+        mask_y(rt + 4 * quad, p, xt[t]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          split_store(sm + kOffA3, sm + kOffA3 + kSzA3, kmaj(4 * quad + e, p, 128), xt[t][e]);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();

@@ -143,5 +143,5 @@ def test_bf16x3_flag_rejected_where_unsupported():
         tq.tsqr_q_create(1000, 100, torch.float32, flags=tq.FLAG_APPLY_BF16X3)
     assert ei.value.code == 5
     with pytest.raises(tq.TsqrError) as ei:
-        tq.tsqr_q_create(1000, 16, torch.float32, flags=8)
+        tq.tsqr_q_create(1000, 16, torch.float32, flags=1 << 10)
     assert ei.value.code == -4
