@@ -283,15 +283,21 @@ def caqr_run(tq, torch, args, steps, warmup, dtype=None, upd=None):
     flops = 4.0 * n ** 3 / 3.0
     upd_ms = st["leaf_apply"][0] / steps
     upd_flops = sum(4.0 * (n - j) * b * (n - j - b) for j in range(0, n, b))
-    eps = {tq.PREC_FP64: 2.0 ** -52, tq.PREC_FP32: 2.0 ** -23, tq.UPDATE_BF16X3: 2.0 ** -16}[upd]
-    if upd == tq.UPDATE_BF16X3:
+    eps = {tq.PREC_FP64: 2.0 ** -52, tq.PREC_FP32: 2.0 ** -23, tq.UPDATE_BF16X3: 2.0 ** -16,
+           tq.UPDATE_TF32X3: 2.0 ** -18}[upd]
+    if upd in (tq.UPDATE_BF16X3, tq.UPDATE_TF32X3):
         peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+        tf32 = upd == tq.UPDATE_TF32X3
+        if tf32:
+            peak *= 1.1 / 2.25  # the measured BF16 peak times the nominal dense TF32 / BF16 ratio
         ach = 3 * upd_flops / (upd_ms / 1e3) / 1e12
         # C (FP32) is read twice and written once per panel: 12 bytes per element.
         upd_bytes = sum(12.0 * (n - j) * (n - j - b) for j in range(0, n, b))
-        roof = {"bound": "tensor", "kernel": "bf16x3_update_kernel (tcgen05, 3 BF16 products per FP32 product)",
+        roof = {"bound": "tensor", "kernel": "split3_update_kernel<%s> (tcgen05, 3 %s products per FP32 product)"
+                % (("true", "TF32") if tf32 else ("false", "BF16")),
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops" + (" x 1.1 / 2.25 (nominal TF32 / BF16)" if tf32 else ""),
                 "hbm_achieved_gbs": upd_bytes / (upd_ms / 1e3) / 1e9,
                 "note": "achieved counts the 3 BF16 products; at b = 64 the update is bound neither by the "
                         "tensor pipe nor by HBM but by each CTA's serial stage / MMA / epilogue steps; the "
@@ -307,10 +313,11 @@ def caqr_run(tq, torch, args, steps, warmup, dtype=None, upd=None):
                 "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": ach / (FP64_PEAK_GFLOPS / 1e3)}
     return {"value": flops / (ms / 1e3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms, "n": n, "b": b,
             "storage": str(dtype).replace("torch.", ""),
-            "update_precision": {tq.PREC_FP64: "fp64", tq.PREC_FP32: "fp32", tq.UPDATE_BF16X3: "3xbf16"}[upd],
+            "update_precision": {tq.PREC_FP64: "fp64", tq.PREC_FP32: "fp32", tq.UPDATE_BF16X3: "3xbf16",
+                                 tq.UPDATE_TF32X3: "3xtf32"}[upd],
             "backward_error": berr, "orthogonality": orth,
             # FP64: 10 n eps sqrt(m); FP32 storage: c sqrt(n) eps with c = 2 (FP32 products) or
-            # 1 (3xBF16 products), orthogonality n eps32 (the tests' bounds).
+            # 1 (3xBF16 / 3xTF32 products), orthogonality n eps32 (the tests' bounds).
             "tolerance": (10 * n * eps * n ** 0.5 if upd == tq.PREC_FP64 else
                           (2.0 if upd == tq.PREC_FP32 else 1.0) * n ** 0.5 * eps),
             "orthogonality_tolerance": 10 * n * eps * n ** 0.5 if upd == tq.PREC_FP64 else n * 2.0 ** -23,
@@ -765,6 +772,8 @@ def ours(args, world, rank, local):
         variants["caqr_fp32_update"] = caqr_run(tq, torch, args, 3, 3, torch.float32, tq.PREC_FP32)
         torch.cuda.empty_cache()
         variants["caqr_3xbf16_update"] = caqr_run(tq, torch, args, 3, 3, torch.float32, tq.UPDATE_BF16X3)
+        torch.cuda.empty_cache()
+        variants["caqr_3xtf32_update"] = caqr_run(tq, torch, args, 3, 3, torch.float32, tq.UPDATE_TF32X3)
         torch.cuda.empty_cache()
     if "batched" in want:
         variants[f"batched_fp32_{args.batched_count}"] = batched_run(

@@ -61,9 +61,13 @@ enum tsqr_status_code {
 enum tsqr_precision {
   TSQR_PREC_FP64 = 0,     /* FP64 storage and arithmetic */
   TSQR_PREC_FP32 = 1,     /* FP32 storage and products; FP64 norms, vectors, tau */
-  TSQR_UPDATE_BF16X3 = 2  /* CAQR only: FP32 storage; leaf-block trailing updates on the
+  TSQR_UPDATE_BF16X3 = 2, /* CAQR only: FP32 storage; leaf-block trailing updates on the
                              tensor cores as three BF16 products (hi*hi + hi*lo + lo*hi)
                              accumulated in FP32; FP64 norms, vectors, tau */
+  TSQR_UPDATE_TF32X3 = 3  /* CAQR only: the same with three TF32 products (kind::tf32);
+                             the split keeps about 21 bits, the tensor cores' FP32
+                             accumulation then limits the result (about 2^-19 of the
+                             sum of |products| measured, against 2^-16 for BF16) */
 };
 
 /* Bits of tsqr_opts_t.flags (TSQR handles only; CAQR takes update_precision instead). */
@@ -92,7 +96,9 @@ enum tsqr_flags {
      I - Y T Y^T, factors the right half, and merges the two T factors; one
      column is the base case.  Same outputs as the default leaf.  n <= 64;
      not with the hybrid or flat tree. */
-  TSQR_FLAG_RECURSIVE_LEAF = 8
+  TSQR_FLAG_RECURSIVE_LEAF = 8,
+  /* As TSQR_FLAG_APPLY_BF16X3 with three TF32 products (TSQR_UPDATE_TF32X3). */
+  TSQR_FLAG_APPLY_TF32X3 = 16
 };
 
 /* Tuning knobs; a zero field means "choose automatically". */
@@ -306,7 +312,8 @@ int tsqr_factor_r_noalloc(int64_t m, int64_t n, double* A, int64_t lda, double* 
  *   triangle (diag(R) >= 0) and the panels' leaf Householder vectors below.
  *   b is the panel width (1 <= b; the last panel may be narrower).
  *   update_precision: TSQR_PREC_FP64 (caqr_factor, double storage), or
- *   TSQR_PREC_FP32 / TSQR_UPDATE_BF16X3 (caqr_factor_f32, float storage).
+ *   TSQR_PREC_FP32 / TSQR_UPDATE_BF16X3 / TSQR_UPDATE_TF32X3 (caqr_factor_f32,
+ *   float storage).
  * For panel j the trailing columns receive (Q_j D_j)^T: first the leaf
  * blocks, then the tree nodes on stacked b-row slices (Section 3.1), then
  * the panel's signs, so rows of R stay consistent without a later fix.

@@ -17,12 +17,13 @@ from ._lib import TsqrBatchOpts, TsqrError, TsqrOpts, check, lib
 
 __all__ = [
     "TsqrError", "QTree", "CaqrQ", "colmajor", "as_colmajor", "tsqr_factor", "tsqr_q_create",
-    "caqr_factor", "caqr_q_create", "Batch", "PREC_FP64", "PREC_FP32", "UPDATE_BF16X3", "FLAG_APPLY_BF16X3", "FLAG_HYBRID_TREE", "FLAG_FLAT_TREE", "FLAG_RECURSIVE_LEAF", "lstsq", "solve_r", "column_norms",
+    "caqr_factor", "caqr_q_create", "Batch", "PREC_FP64", "PREC_FP32", "UPDATE_BF16X3", "UPDATE_TF32X3", "FLAG_APPLY_TF32X3", "FLAG_APPLY_BF16X3", "FLAG_HYBRID_TREE", "FLAG_FLAT_TREE", "FLAG_RECURSIVE_LEAF", "lstsq", "solve_r", "column_norms",
 ]
 
 PREC_FP64 = 0
 PREC_FP32 = 1
 UPDATE_BF16X3 = 2
+UPDATE_TF32X3 = 3
 
 
 def _torch():
@@ -77,6 +78,7 @@ FLAG_APPLY_BF16X3 = 1
 FLAG_HYBRID_TREE = 2
 FLAG_FLAT_TREE = 4
 FLAG_RECURSIVE_LEAF = 8
+FLAG_APPLY_TF32X3 = 16
 
 
 def _opts(leaf_rows: int, arity: int, flags: int = 0):

@@ -164,8 +164,10 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? TSQR_OK : (e == cudaErro
 // fewer than n rows.
 int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t* opts) {
   const int32_t flags = opts ? opts->flags : 0;
-  if (flags & ~(TSQR_FLAG_APPLY_BF16X3 | TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE | TSQR_FLAG_RECURSIVE_LEAF))
+  if (flags & ~(TSQR_FLAG_APPLY_BF16X3 | TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE | TSQR_FLAG_RECURSIVE_LEAF |
+                TSQR_FLAG_APPLY_TF32X3))
     return -4;
+  if ((flags & TSQR_FLAG_APPLY_BF16X3) && (flags & TSQR_FLAG_APPLY_TF32X3)) return -4;
   q->prec = prec;
   q->hybrid = (flags & (TSQR_FLAG_HYBRID_TREE | TSQR_FLAG_FLAT_TREE)) != 0;
   q->rec = (flags & TSQR_FLAG_RECURSIVE_LEAF) != 0;
@@ -240,11 +242,11 @@ int make_plan(tsqr_q_s* q, int64_t m, int64_t n, int32_t prec, const tsqr_opts_t
   while (q->items.back() > 1) q->items.push_back((q->items.back() + q->q - 1) / q->q);
   q->levels = (int32_t)q->items.size() - 1;
   if (n > kMaxN) return TSQR_ERR_UNSUPPORTED;
-  if (flags & TSQR_FLAG_APPLY_BF16X3) {
+  if (flags & (TSQR_FLAG_APPLY_BF16X3 | TSQR_FLAG_APPLY_TF32X3)) {
     // Leaf stage of Q^T C on the tensor cores: FP32 storage, at most 64
     // reflectors, ordinary leaves.
     if (prec != TSQR_PREC_FP32 || n > kBf16x3MaxN || q->hybrid) return TSQR_ERR_UNSUPPORTED;
-    q->upd = TSQR_UPDATE_BF16X3;
+    q->upd = (flags & TSQR_FLAG_APPLY_TF32X3) ? TSQR_UPDATE_TF32X3 : TSQR_UPDATE_BF16X3;
   }
   if (leaf_smem(q->hmax + top) > smax) return TSQR_ERR_UNSUPPORTED;
   if ((int64_t)leaf_apply_smem((int)n, q->es) > smax) return TSQR_ERR_UNSUPPORTED;
@@ -455,8 +457,8 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
       return r;
     }
     if constexpr (sizeof(T) == 4) {
-      if (md == kApplyQT && q->upd == TSQR_UPDATE_BF16X3)
-        r = launch_leaf_update_bf16x3(la, q->status, s);
+      if (md == kApplyQT && (q->upd == TSQR_UPDATE_BF16X3 || q->upd == TSQR_UPDATE_TF32X3))
+        r = launch_leaf_update_split3(la, q->upd == TSQR_UPDATE_TF32X3, q->status, s);
       else
         r = launch_leaf_apply(la, s);
     } else {
@@ -921,7 +923,7 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
   if (n < 1 || n > m) return -2;
   if (b < 1) return -3;
   if (update_precision != TSQR_PREC_FP64 && update_precision != TSQR_PREC_FP32 &&
-      update_precision != TSQR_UPDATE_BF16X3)
+      update_precision != TSQR_UPDATE_BF16X3 && update_precision != TSQR_UPDATE_TF32X3)
     return -4;
   if (opts && opts->flags != 0) return -5;
   caqr_q_s* c = new (std::nothrow) caqr_q_s();
@@ -1145,7 +1147,9 @@ int caqr_factor_f32(int64_t m, int64_t n, float* A, int64_t lda, int64_t b, int3
   if (m > 0 && n > 0 && !A) return -3;
   if (lda < (m > 1 ? m : 1)) return -4;
   if (b < 1) return -5;
-  if (update_precision != TSQR_PREC_FP32 && update_precision != TSQR_UPDATE_BF16X3) return -6;
+  if (update_precision != TSQR_PREC_FP32 && update_precision != TSQR_UPDATE_BF16X3 &&
+      update_precision != TSQR_UPDATE_TF32X3)
+    return -6;
   if (m == 0 || n == 0) return TSQR_OK;
   return caqr_factor_any(m, n, A, lda, b, update_precision, opts, q, stream);
 }

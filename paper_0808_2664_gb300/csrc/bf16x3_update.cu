@@ -30,18 +30,10 @@ namespace tsqr {
 namespace {
 
 constexpr int kUN = 128;       // columns of C per CTA (MMA M of step 1, N of step 3)
-constexpr int kUChunk = 64;    // leaf rows staged per step-1 chunk
 constexpr int kUThreads = 256; // eight warps; warps w and w+4 share TMEM lane quarter w % 4
 constexpr int kUNp = 64;       // reflector count padded to the MMA N / K granularity
 constexpr int kTmemCols = 256; // D1 at columns [0, 64), D2 at [64, 192)
 constexpr long long kPollLimit = 1ll << 24;
-
-// Byte offset of element (r, k) in a K-major no-swizzle tile with R rows:
-// core matrices of 8 rows x 8 BF16 (128 contiguous bytes), R/8 of them per
-// 8-column K slab, K slabs one after another.
-__device__ __forceinline__ uint32_t kmaj(int r, int k, int R) {
-  return (uint32_t)((((k >> 3) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
-}
 
 // Shared-memory matrix descriptor (no swizzle): start address, leading byte
 // offset (between K-adjacent core matrices), stride byte offset (between
@@ -49,19 +41,6 @@ __device__ __forceinline__ uint32_t kmaj(int r, int k, int R) {
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
-}
-
-// Instruction descriptor for kind::f16: FP32 D, BF16 A and B, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -95,13 +74,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void split_store(unsigned char* hi_base, unsigned char* lo_base, uint32_t off, float x) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-  *reinterpret_cast<__nv_bfloat16*>(hi_base + off) = h;
-  *reinterpret_cast<__nv_bfloat16*>(lo_base + off) = l;
-}
-
 struct Bf16x3Args {
   const float* Y;  // factored panel storage: leaf reflectors
   int64_t ldy;
@@ -117,35 +89,123 @@ struct Bf16x3Args {
   int vec;  // 16-byte loads allowed (C, Y, ldc, ldy, h aligned)
 };
 
-// Shared memory map (bytes from a 1024-aligned base).  Step 1's operand
-// tiles are double-buffered so the next chunk is staged while the tensor
-// cores work on the current one.
-constexpr uint32_t kSzA1 = kUN * kUChunk * 2;          // C^T chunk, one BF16 term: 16 KB
-constexpr uint32_t kSzB1 = kUNp * kUChunk * 2;         // Y chunk, one term: 8 KB
-constexpr uint32_t kOffA1 = 0;                         // [buffer][hi | lo]
-constexpr uint32_t kOffB1 = kOffA1 + 4 * kSzA1;        // [buffer][hi | lo]
-constexpr uint32_t kSzA3 = 128 * kUNp * 2;             // Y row tile, one term: 16 KB
-constexpr uint32_t kOffA3 = kOffB1 + 4 * kSzB1;
-constexpr uint32_t kSzB3 = kUN * kUNp * 2;             // W', one term: 16 KB
-constexpr uint32_t kOffB3 = kOffA3 + 2 * kSzA3;
-constexpr uint32_t kOffT = kOffB3 + 2 * kSzB3;         // T: 64x64 fp32
-constexpr uint32_t kOffBar = kOffT + kUNp * kUNp * 4;  // mbarrier (8 B) + tmem address (4 B)
-constexpr uint32_t kSmemBytes = kOffBar + 64 + 1024;   // + alignment slack
+// The two split-product forms.  Each FP32 operand x is split into a high
+// and a low term of the MMA input type and every product is formed as
+// hi*hi + hi*lo + lo*hi:
+//   three BF16 products (kind::f16, BF16 A and B): about 2^-16 relative
+//   error per product;
+//   three TF32 products (kind::tf32): about 2^-21 from the split, below the
+//   floor of the tensor cores' FP32 accumulation (about 2^-19 measured).
+// Both input types have 16-byte core-matrix rows (8 BF16 or 4 TF32) and 32
+// bytes of K per MMA instruction (16 BF16 or 8 TF32), so the descriptors and
+// K steps are the same; TF32 tiles take twice the bytes, so its step-1 chunks
+// are 32 rows and its step-3 tiles reuse the step-1 region.
+// Shared memory map (bytes from a 1024-aligned base): step 1's operand tiles
+// are double-buffered ([buffer][hi | lo]) so the next chunk is staged while
+// the tensor cores work on the current one; then step 3's Y row tile and W'.
+template <bool kTF32>
+struct Split3 {
+  static constexpr uint32_t ES = kTF32 ? 4 : 2;    // bytes per element
+  static constexpr uint32_t EPR = 16 / ES;          // elements per 16-byte core-matrix row
+  static constexpr uint32_t KI = kTF32 ? 8 : 16;    // K per MMA instruction
+  static constexpr int CHUNK = kTF32 ? 32 : 64;     // leaf rows per step-1 chunk
+  static constexpr uint32_t SzA1 = kUN * CHUNK * ES;  // C^T chunk, one term
+  static constexpr uint32_t SzB1 = kUNp * CHUNK * ES; // Y chunk, one term
+  static constexpr uint32_t SzA3 = 128 * kUNp * ES;   // Y row tile, one term
+  static constexpr uint32_t SzB3 = kUN * kUNp * ES;   // W', one term
+  static constexpr uint32_t OffA1 = 0;
+  static constexpr uint32_t OffB1 = OffA1 + 4 * SzA1;
+  static constexpr uint32_t End1 = OffB1 + 4 * SzB1;
+  static constexpr uint32_t OffA3 = kTF32 ? 0 : End1;  // TF32: over the finished step-1 tiles
+  static constexpr uint32_t OffB3 = OffA3 + 2 * SzA3;
+  static constexpr uint32_t End3 = OffB3 + 2 * SzB3;
+  static constexpr uint32_t OffT = End1 > End3 ? End1 : End3;  // T: 64 x 64 FP32
+  static constexpr uint32_t OffBar = OffT + kUNp * kUNp * 4;   // mbarrier (8 B) + TMEM address (4 B)
+  static constexpr uint32_t SmemBytes = OffBar + 64 + 1024;    // + alignment slack
 
-// Four consecutive BF16 hi (and lo) terms of x[0..3] at byte offset off (8-byte aligned).
-__device__ __forceinline__ void split_store4(unsigned char* hi_base, unsigned char* lo_base, uint32_t off,
-                                             const float* x) {
-  __nv_bfloat16 h[4], l[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    h[e] = __float2bfloat16_rn(x[e]);
-    l[e] = __float2bfloat16_rn(x[e] - __bfloat162float(h[e]));
+  // Byte offset of element (r, k) in a K-major no-swizzle tile with R rows:
+  // core matrices of 8 rows x 16 bytes (128 contiguous bytes), R/8 of them
+  // per K slab of EPR elements, K slabs one after another.
+  static __device__ __forceinline__ uint32_t kmaj(int r, int k, int R) {
+    return (uint32_t)(((((uint32_t)k / EPR) * (R >> 3) + (r >> 3)) << 7) + ((r & 7) << 4) + ((uint32_t)k % EPR) * ES);
   }
-  *reinterpret_cast<uint2*>(hi_base + off) = *reinterpret_cast<const uint2*>(h);
-  *reinterpret_cast<uint2*>(lo_base + off) = *reinterpret_cast<const uint2*>(l);
-}
 
-__global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args a) {
+  // Instruction descriptor: FP32 D; A and B BF16 (1) or TF32 (2); both K-major.
+  static __host__ __device__ constexpr uint32_t idesc(int M, int N) {
+    return (1u << 4) | ((kTF32 ? 2u : 1u) << 7) | ((kTF32 ? 2u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+  }
+
+  static __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    if constexpr (kTF32) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    } else {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+          "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+    }
+  }
+
+  // TF32 rounding of x (round to nearest, ties away), as an FP32 bit pattern.
+  static __device__ __forceinline__ uint32_t tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+  }
+
+  // hi and lo terms of one value at byte offset off.
+  static __device__ __forceinline__ void store1(unsigned char* hi_base, unsigned char* lo_base, uint32_t off,
+                                                float x) {
+    if constexpr (kTF32) {
+      const uint32_t h = tf32(x);
+      const uint32_t l = tf32(x - __uint_as_float(h));
+      *reinterpret_cast<uint32_t*>(hi_base + off) = h;
+      *reinterpret_cast<uint32_t*>(lo_base + off) = l;
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      *reinterpret_cast<__nv_bfloat16*>(hi_base + off) = h;
+      *reinterpret_cast<__nv_bfloat16*>(lo_base + off) = l;
+    }
+  }
+
+  // Four consecutive K elements x[0..3] at byte offset off (4 ES-aligned).
+  static __device__ __forceinline__ void store4(unsigned char* hi_base, unsigned char* lo_base, uint32_t off,
+                                                const float* x) {
+    if constexpr (kTF32) {
+      uint4 h, l;
+      h.x = tf32(x[0]);
+      h.y = tf32(x[1]);
+      h.z = tf32(x[2]);
+      h.w = tf32(x[3]);
+      l.x = tf32(x[0] - __uint_as_float(h.x));
+      l.y = tf32(x[1] - __uint_as_float(h.y));
+      l.z = tf32(x[2] - __uint_as_float(h.z));
+      l.w = tf32(x[3] - __uint_as_float(h.w));
+      *reinterpret_cast<uint4*>(hi_base + off) = h;
+      *reinterpret_cast<uint4*>(lo_base + off) = l;
+    } else {
+      __nv_bfloat16 h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        h[e] = __float2bfloat16_rn(x[e]);
+        l[e] = __float2bfloat16_rn(x[e] - __bfloat162float(h[e]));
+      }
+      *reinterpret_cast<uint2*>(hi_base + off) = *reinterpret_cast<const uint2*>(h);
+      *reinterpret_cast<uint2*>(lo_base + off) = *reinterpret_cast<const uint2*>(l);
+    }
+  }
+};
+
+template <bool kTF32>
+__global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args a) {
+  using S3 = Split3<kTF32>;
+  constexpr int kUChunk = S3::CHUNK;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
@@ -160,16 +220,16 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
   const int hl = (leaf == a.nleaves - 1) ? (int)(a.m - r0) : (int)a.h;
   const float* Yg = a.Y + r0;
   float* Cg = a.C + r0 + k0 * a.ldc;
-  float* Ts = reinterpret_cast<float*>(sm + kOffT);
-  const uint32_t mbar = sbase + kOffBar;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 8);
+  float* Ts = reinterpret_cast<float*>(sm + S3::OffT);
+  const uint32_t mbar = sbase + S3::OffBar;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + S3::OffBar + 8);
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < 32) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + kOffBar + 8),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + S3::OffBar + 8),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -217,8 +277,8 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
   };
   auto stage1 = [&](int ch, int buf) {
     const int rb = ch * kUChunk;
-    unsigned char* ahi = sm + kOffA1 + (2 * buf) * kSzA1;
-    unsigned char* bhi = sm + kOffB1 + (2 * buf) * kSzB1;
+    unsigned char* ahi = sm + S3::OffA1 + (2 * buf) * S3::SzA1;
+    unsigned char* bhi = sm + S3::OffB1 + (2 * buf) * S3::SzB1;
     // All of this thread's global loads for the chunk are issued before any
     // of them is converted, so that their latencies overlap.
     constexpr int kCPer = kUN * (kUChunk / 4) / kUThreads, kYPer = kUNp * (kUChunk / 4) / kUThreads;
@@ -243,37 +303,37 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
     for (int t = 0; t < kCPer; ++t) {
       const int idx = tid + t * kUThreads;
       const int quad = idx % (kUChunk / 4), c = idx / (kUChunk / 4);
-      split_store4(ahi, ahi + kSzA1, kmaj(c, 4 * quad, kUN), xc[t]);
+      S3::store4(ahi, ahi + S3::SzA1, S3::kmaj(c, 4 * quad, kUN), xc[t]);
     }
 #pragma unroll
     for (int t = 0; t < kYPer; ++t) {
       const int idx = tid + t * kUThreads;
       const int quad = idx % (kUChunk / 4), p = idx / (kUChunk / 4);
       mask_y(rb + 4 * quad, p, xy[t]);
-      split_store4(bhi, bhi + kSzB1, kmaj(p, 4 * quad, kUNp), xy[t]);
+      S3::store4(bhi, bhi + S3::SzB1, S3::kmaj(p, 4 * quad, kUNp), xy[t]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   };
   auto issue1 = [&](int ch, int buf) {
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      constexpr uint32_t id1 = idesc_bf16(kUN, kUNp);
-      const uint32_t A = sbase + kOffA1 + (2 * buf) * kSzA1, B = sbase + kOffB1 + (2 * buf) * kSzB1;
+      constexpr uint32_t id1 = S3::idesc(kUN, kUNp);
+      const uint32_t A = sbase + S3::OffA1 + (2 * buf) * S3::SzA1, B = sbase + S3::OffB1 + (2 * buf) * S3::SzB1;
 #pragma unroll
-      for (int s = 0; s < kUChunk / 16; ++s) {
+      for (int s = 0; s < kUChunk / (int)S3::KI; ++s) {
         const uint32_t aoff = (uint32_t)s * kUN * 32, boff = (uint32_t)s * kUNp * 32;
-        const uint64_t ahi = sdesc(A + aoff, kUN * 16, 128), alo = sdesc(A + kSzA1 + aoff, kUN * 16, 128);
-        const uint64_t bhi = sdesc(B + boff, kUNp * 16, 128), blo = sdesc(B + kSzB1 + boff, kUNp * 16, 128);
-        mma_bf16(d1, ahi, bhi, id1, (ch > 0 || s > 0) ? 1u : 0u);
-        mma_bf16(d1, ahi, blo, id1, 1u);
-        mma_bf16(d1, alo, bhi, id1, 1u);
+        const uint64_t ahi = sdesc(A + aoff, kUN * 16, 128), alo = sdesc(A + S3::SzA1 + aoff, kUN * 16, 128);
+        const uint64_t bhi = sdesc(B + boff, kUNp * 16, 128), blo = sdesc(B + S3::SzB1 + boff, kUNp * 16, 128);
+        S3::mma(d1, ahi, bhi, id1, (ch > 0 || s > 0) ? 1u : 0u);
+        S3::mma(d1, ahi, blo, id1, 1u);
+        S3::mma(d1, alo, bhi, id1, 1u);
       }
       mma_commit(mbar);
     }
     ++commits;
   };
 
-  // ---- Step 1: W^T = C^T Y over the leaf rows, 64 rows per chunk; chunk
+  // ---- Step 1: W^T = C^T Y over the leaf rows, kUChunk rows per chunk; chunk
   // ch+1 is staged while the MMAs of chunk ch run.
   const int nchunks = (hl + kUChunk - 1) / kUChunk;
   stage1(0, 0);
@@ -314,7 +374,7 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
     }
 #pragma unroll
     for (int q = 0; q < 32; q += 4)
-      split_store4(sm + kOffB3, sm + kOffB3 + kSzB3, kmaj(c, 32 * half + q, kUN), wp + q);
+      S3::store4(sm + S3::OffB3, sm + S3::OffB3 + S3::SzB3, S3::kmaj(c, 32 * half + q, kUN), wp + q);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -342,24 +402,24 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
         mask_y(rt + 4 * quad, p, xt[t]);
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          split_store(sm + kOffA3, sm + kOffA3 + kSzA3, kmaj(4 * quad + e, p, 128), xt[t][e]);
+          S3::store1(sm + S3::OffA3, sm + S3::OffA3 + S3::SzA3, S3::kmaj(4 * quad + e, p, 128), xt[t][e]);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      constexpr uint32_t id3 = idesc_bf16(128, kUN);
+      constexpr uint32_t id3 = S3::idesc(128, kUN);
 #pragma unroll
-      for (int s = 0; s < kUNp / 16; ++s) {
+      for (int s = 0; s < kUNp / (int)S3::KI; ++s) {
         const uint32_t aoff = (uint32_t)s * 128 * 32, boff = (uint32_t)s * kUN * 32;
-        const uint64_t ahi = sdesc(sbase + kOffA3 + aoff, 128 * 16, 128);
-        const uint64_t alo = sdesc(sbase + kOffA3 + kSzA3 + aoff, 128 * 16, 128);
-        const uint64_t bhi = sdesc(sbase + kOffB3 + boff, kUN * 16, 128);
-        const uint64_t blo = sdesc(sbase + kOffB3 + kSzB3 + boff, kUN * 16, 128);
-        mma_bf16(d2, ahi, bhi, id3, s > 0 ? 1u : 0u);
-        mma_bf16(d2, ahi, blo, id3, 1u);
-        mma_bf16(d2, alo, bhi, id3, 1u);
+        const uint64_t ahi = sdesc(sbase + S3::OffA3 + aoff, 128 * 16, 128);
+        const uint64_t alo = sdesc(sbase + S3::OffA3 + S3::SzA3 + aoff, 128 * 16, 128);
+        const uint64_t bhi = sdesc(sbase + S3::OffB3 + boff, kUN * 16, 128);
+        const uint64_t blo = sdesc(sbase + S3::OffB3 + S3::SzB3 + boff, kUN * 16, 128);
+        S3::mma(d2, ahi, bhi, id3, s > 0 ? 1u : 0u);
+        S3::mma(d2, ahi, blo, id3, 1u);
+        S3::mma(d2, alo, bhi, id3, 1u);
       }
       mma_commit(mbar);
     }
@@ -398,7 +458,7 @@ __global__ void __launch_bounds__(kUThreads, 1) bf16x3_update_kernel(Bf16x3Args 
 
 }  // namespace
 
-cudaError_t launch_leaf_update_bf16x3(const LeafApplyArgs<float>& la, int* status, cudaStream_t s) {
+cudaError_t launch_leaf_update_split3(const LeafApplyArgs<float>& la, bool tf32, int* status, cudaStream_t s) {
   if (la.nleaves <= 0 || la.k <= 0 || la.n <= 0) return cudaSuccess;
   if (la.n > kBf16x3MaxN) return cudaErrorInvalidValue;
   Bf16x3Args a;
@@ -417,12 +477,20 @@ cudaError_t launch_leaf_update_bf16x3(const LeafApplyArgs<float>& la, int* statu
            la.h % 4 == 0)
               ? 1
               : 0;
-  cudaError_t e = cudaFuncSetAttribute(bf16x3_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-  if (e != cudaSuccess) return e;
   const int64_t kchunks = (la.k + kUN - 1) / kUN;
   if (kchunks > 65535 || la.nleaves > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)la.nleaves, (unsigned)kchunks);
-  bf16x3_update_kernel<<<grid, kUThreads, kSmemBytes, s>>>(a);
+  if (tf32) {
+    constexpr uint32_t smem = Split3<true>::SmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(split3_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    split3_update_kernel<true><<<grid, kUThreads, smem, s>>>(a);
+  } else {
+    constexpr uint32_t smem = Split3<false>::SmemBytes;
+    cudaError_t e = cudaFuncSetAttribute(split3_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    split3_update_kernel<false><<<grid, kUThreads, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

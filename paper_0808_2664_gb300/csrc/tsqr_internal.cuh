@@ -156,8 +156,9 @@ cudaError_t launch_leaf_apply(const LeafApplyArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_node_apply(const NodeApplyArgs<T>& a, cudaStream_t s);
 
-// C <- C - Y T^T Y^T C per leaf with 3xBF16 tcgen05 products (FP32 storage, n <= 64).
-cudaError_t launch_leaf_update_bf16x3(const LeafApplyArgs<float>& a, int* status, cudaStream_t s);
+// C <- C - Y T^T Y^T C per leaf with three split products on tcgen05 (FP32
+// storage, n <= 64): BF16 terms (kind::f16) or, with tf32, TF32 terms.
+cudaError_t launch_leaf_update_split3(const LeafApplyArgs<float>& a, bool tf32, int* status, cudaStream_t s);
 
 // d = sign(diag Rroot) (sign(0) = +1); Rout = D * triu(Rroot), ldr.  Entries
 // below the diagonal of Rout are zeroed when zero_lower, left alone otherwise.

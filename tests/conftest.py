@@ -18,6 +18,12 @@ EPS32 = 2.0 ** -23
 # (hi*hi + hi*lo + lo*hi): the dropped lo*lo term and the two split residuals
 # are each below 2^-16 of |x y|.
 EPS_BF16X3 = 2.0 ** -16
+# The same with three TF32 products (11-bit significands): the split itself
+# leaves about 2^-21 of |x y|, but the tensor cores' FP32 accumulation sets
+# the floor -- measured on this GPU at 1.5e-6 of the sum of |terms| for a
+# 512-row leaf, with both splits; 2^-18 covers it by a factor of five and is
+# still about 2^-7 below the error of a dropped cross term (2^-11).
+EPS_TF32X3 = 2.0 ** -18
 
 
 def fp64_tol(m: int, n: int) -> float:

@@ -1,11 +1,13 @@
-"""CAQR and single trailing updates with FP32 storage: FP32 products and 3xBF16
-tensor-core (tcgen05) products, reflector generation in FP64 in both forms.
+"""CAQR and single trailing updates with FP32 storage: FP32 products and 3xBF16 or
+3xTF32 tensor-core (tcgen05) products, reflector generation in FP64 in every form.
 
 Bounds (derived from the product arithmetic, not from measurements):
   * one trailing update C <- (I - Y T^T Y^T) C (Section 3.1) is compared with
     the oracle's FP64 Q^T C entry by entry:
         |dC_ij| <= 2 eps (|Y| |T|^T |Y|^T |C|)_ij,
-    eps = 2^-16 for three BF16 products, 2^-23 for FP32 products, with the
+    eps = 2^-16 for three BF16 products, 2^-18 for three TF32 products (whose
+    error floor is the tensor cores' FP32 accumulation), 2^-23 for FP32
+    products, with the
     oracle's Y and T.  A 3xBF16 product loses at most about 3 * 2^-16 of
     |x y|; a kernel that dropped its hi*lo or lo*hi term would lose about
     2^-9 of it, which puts such errors at 20 to 50 times this bound (an
@@ -22,7 +24,7 @@ Bounds (derived from the product arithmetic, not from measurements):
 import numpy as np
 import pytest
 
-from conftest import EPS32, EPS_BF16X3, assert_colwise_close, caqr_mixed_tol
+from conftest import EPS32, EPS_BF16X3, EPS_TF32X3, assert_colwise_close, caqr_mixed_tol
 from paper_0808_2664_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -48,17 +50,23 @@ def f32_exact(X):
 def bounds(upd, n):
     if upd == "fp32":
         return caqr_mixed_tol(n, EPS32, C_FP32)
+    if upd == "tf32x3":
+        return caqr_mixed_tol(n, EPS_TF32X3, C_BF16X3)
     return caqr_mixed_tol(n, EPS_BF16X3, C_BF16X3)
 
 
-@pytest.mark.parametrize("upd", ["fp32", "bf16x3"])
+PREC = {"fp32": tq.PREC_FP32, "bf16x3": tq.UPDATE_BF16X3, "tf32x3": tq.UPDATE_TF32X3}
+FLAGS = {"fp32": 0, "bf16x3": tq.FLAG_APPLY_BF16X3, "tf32x3": tq.FLAG_APPLY_TF32X3}
+EPS = {"fp32": EPS32, "bf16x3": EPS_BF16X3, "tf32x3": EPS_TF32X3}
+
+
+@pytest.mark.parametrize("upd", ["fp32", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("m,n,b", [(256, 256, 64), (1000, 300, 64), (777, 200, 48), (2048, 128, 32), (1536, 1024, 64)])
 def test_caqr_fp32_storage_matches_oracle(oracle_mod, upd, m, n, b):
     A = f32_exact(inputs.uniform(m, n, seed=9000 + m + n))
     Qo, Ro = oracle_mod.qr(A)
     Ad = dev32(A)
-    prec = tq.PREC_FP32 if upd == "fp32" else tq.UPDATE_BF16X3
-    q = tq.caqr_factor(Ad, b=b, update_precision=prec)
+    q = tq.caqr_factor(Ad, b=b, update_precision=PREC[upd])
     Q = q.form_q().double().cpu().numpy()
     assert q.sync_status() == 0
     R = np.triu(Ad.double().cpu().numpy()[:n, :n])
@@ -89,8 +97,7 @@ def test_bf16x3_update_close_to_fp32_update():
 def _single_update(oracle_mod, m, n, k, h, upd, seed):
     A = f32_exact(inputs.gaussian(m, n, seed))
     C = f32_exact(inputs.gaussian(m, k, seed + 1))
-    flags = tq.FLAG_APPLY_BF16X3 if upd == "bf16x3" else 0
-    q = tq.tsqr_q_create(m, n, torch.float32, leaf_rows=h, arity=2, flags=flags)
+    q = tq.tsqr_q_create(m, n, torch.float32, leaf_rows=h, arity=2, flags=FLAGS[upd])
     q.refactor(dev32(A))
     Cd = dev32(C)
     q.apply_qt(Cd)
@@ -101,7 +108,7 @@ def _single_update(oracle_mod, m, n, k, h, upd, seed):
     return A, C, q, f, got, want
 
 
-@pytest.mark.parametrize("upd", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("upd", ["bf16x3", "tf32x3", "fp32"])
 @pytest.mark.parametrize("m,k", [(512, 256), (450, 200), (130, 64), (512, 1000)])
 def test_single_leaf_update_elementwise(oracle_mod, upd, m, k):
     """One leaf (the panel is one row block): its reflectors are the oracle's, so every
@@ -112,7 +119,7 @@ def test_single_leaf_update_elementwise(oracle_mod, upd, m, k):
     Y = oracle_mod.unit_lower(f)
     T = oracle_mod.larft(f)
     rhs = np.abs(Y) @ (np.abs(T).T @ (np.abs(Y).T @ np.abs(C)))
-    eps = EPS_BF16X3 if upd == "bf16x3" else EPS32
+    eps = EPS[upd]
     # FP32 storage of C' adds one rounding of each result entry.
     bound = 2 * eps * rhs + EPS32 * np.abs(want)
     ratio = np.abs(got - want) / bound
@@ -121,14 +128,14 @@ def test_single_leaf_update_elementwise(oracle_mod, upd, m, k):
     q.destroy()
 
 
-@pytest.mark.parametrize("upd", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("upd", ["bf16x3", "tf32x3", "fp32"])
 @pytest.mark.parametrize("m,n,k,h", [(4096, 64, 300, 512), (3000, 32, 129, 256), (20000, 64, 128, 512)])
 def test_multi_leaf_update_columnwise(oracle_mod, upd, m, n, k, h):
     """Several leaves and a binary tree: the top n rows of Q^T C (the unique part)
     against the oracle, column-wise; the rest keeps each column's norm."""
     A, C, q, f, got, want = _single_update(oracle_mod, m, n, k, h, upd, 7300 + m + k)
     assert q.info()["leaves"] > 1
-    eps = EPS_BF16X3 if upd == "bf16x3" else EPS32
+    eps = EPS[upd]
     tol = 2 * eps + 4 * n * EPS32  # the update, plus the FP32 tree levels
     assert_colwise_close(got[:n], want[:n], tol, "QtC")
     np.testing.assert_allclose(np.linalg.norm(got, axis=0), np.linalg.norm(C, axis=0), rtol=tol)
@@ -145,3 +152,4 @@ def test_bf16x3_flag_rejected_where_unsupported():
     with pytest.raises(tq.TsqrError) as ei:
         tq.tsqr_q_create(1000, 16, torch.float32, flags=1 << 10)
     assert ei.value.code == -4
+
