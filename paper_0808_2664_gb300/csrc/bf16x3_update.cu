@@ -19,10 +19,12 @@
 // wait on that mbarrier gives up after a bounded number of polls (latching
 // the status word's timeout bit) so the kernel can never hang; tensor memory
 // is always released before the CTA exits.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "tsqr_internal.cuh"
 
@@ -60,6 +62,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+
+// One more expected arrival carrying `bytes` of asynchronous copies.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// 2-D tiled copy global -> shared through the tensor-memory-access engine;
+// c0 is the innermost (row) coordinate, completion counted on mbar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(mbar)
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -116,11 +133,21 @@ struct Split3 {
   static constexpr uint32_t OffA1 = 0;
   static constexpr uint32_t OffB1 = OffA1 + 4 * SzA1;
   static constexpr uint32_t End1 = OffB1 + 4 * SzB1;
-  static constexpr uint32_t OffA3 = kTF32 ? 0 : End1;  // TF32: over the finished step-1 tiles
+  // Raw FP32 chunks of C (CHUNK rows x kUN columns) and Y (CHUNK x kUNp),
+  // written by the tensor-memory-access engine, two buffers.
+  static constexpr uint32_t RawC = (uint32_t)CHUNK * kUN * 4;
+  static constexpr uint32_t RawY = (uint32_t)CHUNK * kUNp * 4;
+  static constexpr uint32_t OffRaw = End1;
+  static constexpr uint32_t EndRaw = OffRaw + 2 * (RawC + RawY);
+  // Step 3's tiles reuse finished step-1 storage: the raw buffers (BF16) or
+  // the split tiles and raw buffers (TF32).
+  static constexpr uint32_t OffA3 = kTF32 ? 0 : OffRaw;
   static constexpr uint32_t OffB3 = OffA3 + 2 * SzA3;
   static constexpr uint32_t End3 = OffB3 + 2 * SzB3;
-  static constexpr uint32_t OffT = End1 > End3 ? End1 : End3;  // T: 64 x 64 FP32
-  static constexpr uint32_t OffBar = OffT + kUNp * kUNp * 4;   // mbarrier (8 B) + TMEM address (4 B)
+  static constexpr uint32_t OffT = EndRaw > End3 ? EndRaw : End3;  // T: 64 x 64 FP32
+  // MMA mbarrier (8 B), TMEM address (4 B), two chunk mbarriers (8 B each).
+  static constexpr uint32_t OffBar = OffT + kUNp * kUNp * 4;
+  static_assert(OffBar + 64 + 1024 <= 227 * 1024, "shared memory of the split-product update");
   static constexpr uint32_t SmemBytes = OffBar + 64 + 1024;    // + alignment slack
 
   // Byte offset of element (r, k) in a K-major no-swizzle tile with R rows:
@@ -202,8 +229,12 @@ struct Split3 {
   }
 };
 
-template <bool kTF32>
-__global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args a) {
+// kTMA: step 1's C and Y chunks arrive through cp.async.bulk.tensor (tmC,
+// tmY: maps of C and Y with boxes of CHUNK rows), two chunks ahead of the one
+// being converted; otherwise each thread loads its share of the chunk.
+template <bool kTF32, bool kTMA>
+__global__ void __launch_bounds__(kUThreads, 1)
+    split3_update_kernel(Bf16x3Args a, const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmY) {
   using S3 = Split3<kTF32>;
   constexpr int kUChunk = S3::CHUNK;
   extern __shared__ unsigned char smem_raw[];
@@ -223,9 +254,14 @@ __global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args 
   float* Ts = reinterpret_cast<float*>(sm + S3::OffT);
   const uint32_t mbar = sbase + S3::OffBar;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + S3::OffBar + 8);
+  const uint32_t mraw = sbase + S3::OffBar + 16;  // chunk buffer b: mraw + 8 b
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    if (kTMA) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mraw) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mraw + 8) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid < 32) {
@@ -247,13 +283,31 @@ __global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args 
   const uint32_t d1 = tmem, d2 = tmem + kUNp;
   uint32_t commits = 0, waited = 0;  // tcgen05.commit k completes mbarrier phase k
   bool ok = true;
+  // Every wait ends with a CTA-wide agreement on `ok`, so that the threads
+  // never take different paths around the barriers that follow.
   auto wait_next = [&]() {
     if (mbar_wait(mbar, waited & 1)) {
       ++waited;
     } else {
       ok = false;
-      if (tid == 0) atomicOr(a.status, kStatusTimeout);
+      atomicOr(a.status, kStatusTimeout);
     }
+    ok = __syncthreads_and(ok) != 0;
+  };
+  // Raw chunk buffers: copies issued / waited for per buffer (the same on
+  // every thread).
+  uint32_t raw_issued[2] = {0u, 0u}, raw_done[2] = {0u, 0u};
+  auto issue_raw = [&](int ch) {
+    const int b = ch & 1;
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(mraw + 8 * b, S3::RawC + S3::RawY);
+      const uint32_t dst = sbase + S3::OffRaw + (uint32_t)b * (S3::RawC + S3::RawY);
+      const int row = (int)(r0 + (int64_t)ch * kUChunk);
+      tma_load_2d(dst, &tmC, row, (int)k0, mraw + 8 * b);
+      tma_load_2d(dst + S3::RawC, &tmY, row, 0, mraw + 8 * b);
+    }
+    ++raw_issued[b];
   };
   // Four rows r..r+3 of column col of a column-major FP32 matrix (rows
   // beyond hl are zero): one 16-byte load when aligned and complete.
@@ -279,9 +333,45 @@ __global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args 
     const int rb = ch * kUChunk;
     unsigned char* ahi = sm + S3::OffA1 + (2 * buf) * S3::SzA1;
     unsigned char* bhi = sm + S3::OffB1 + (2 * buf) * S3::SzB1;
+    constexpr int kCPer = kUN * (kUChunk / 4) / kUThreads, kYPer = kUNp * (kUChunk / 4) / kUThreads;
+    if constexpr (kTMA) {
+      // The chunk's raw FP32 tiles ([column][row], CHUNK rows per column)
+      // are in buffer ch & 1 once its mbarrier phase completes; rows beyond
+      // the leaf are zeroed here (they belong to the next leaf, or are the
+      // copy's zero fill past the matrix).
+      const int b = ch & 1;
+      if (mbar_wait(mraw + 8 * b, raw_done[b] & 1)) {
+        ++raw_done[b];
+      } else {
+        ok = false;
+        atomicOr(a.status, kStatusTimeout);
+      }
+      if (!ok) return;
+      const float* rc = reinterpret_cast<const float*>(sm + S3::OffRaw + (uint32_t)b * (S3::RawC + S3::RawY));
+      const float* ry = rc + S3::RawC / 4;
+#pragma unroll
+      for (int t = 0; t < kCPer; ++t) {
+        const int idx = tid + t * kUThreads;
+        const int quad = idx % (kUChunk / 4), c = idx / (kUChunk / 4);
+        const float4 v = *reinterpret_cast<const float4*>(rc + c * kUChunk + 4 * quad);
+        float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (rb + 4 * quad + e >= hl) x[e] = 0.f;
+        S3::store4(ahi, ahi + S3::SzA1, S3::kmaj(c, 4 * quad, kUN), x);
+      }
+#pragma unroll
+      for (int t = 0; t < kYPer; ++t) {
+        const int idx = tid + t * kUThreads;
+        const int quad = idx % (kUChunk / 4), p = idx / (kUChunk / 4);
+        const float4 v = *reinterpret_cast<const float4*>(ry + p * kUChunk + 4 * quad);
+        float x[4] = {v.x, v.y, v.z, v.w};
+        mask_y(rb + 4 * quad, p, x);
+        S3::store4(bhi, bhi + S3::SzB1, S3::kmaj(p, 4 * quad, kUNp), x);
+      }
+    } else {
     // All of this thread's global loads for the chunk are issued before any
     // of them is converted, so that their latencies overlap.
-    constexpr int kCPer = kUN * (kUChunk / 4) / kUThreads, kYPer = kUNp * (kUChunk / 4) / kUThreads;
     float xc[kCPer][4], xy[kYPer][4];
 #pragma unroll
     for (int t = 0; t < kCPer; ++t) {
@@ -312,6 +402,7 @@ __global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args 
       mask_y(rb + 4 * quad, p, xy[t]);
       S3::store4(bhi, bhi + S3::SzB1, S3::kmaj(p, 4 * quad, kUNp), xy[t]);
     }
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   };
   auto issue1 = [&](int ch, int buf) {
@@ -334,14 +425,26 @@ __global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args 
   };
 
   // ---- Step 1: W^T = C^T Y over the leaf rows, kUChunk rows per chunk; chunk
-  // ch+1 is staged while the MMAs of chunk ch run.
+  // ch+1 is staged while the MMAs of chunk ch run (and, with kTMA, the raw
+  // tiles of chunks ch+1 and ch+2 are in flight meanwhile).
   const int nchunks = (hl + kUChunk - 1) / kUChunk;
+  if constexpr (kTMA) {
+    issue_raw(0);
+    if (nchunks > 1) issue_raw(1);
+  }
   stage1(0, 0);
-  __syncthreads();
-  issue1(0, 0);
+  ok = __syncthreads_and(ok) != 0;
+  if (ok) {
+    if constexpr (kTMA)
+      if (nchunks > 2) issue_raw(2);  // raw buffer 0 is converted
+    issue1(0, 0);
+  }
   for (int ch = 1; ch < nchunks && ok; ++ch) {
     stage1(ch, ch & 1);  // buffer ch&1 was read by chunk ch-2, already complete
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    if constexpr (kTMA)
+      if (ch + 2 < nchunks) issue_raw(ch + 2);  // raw buffer ch&1 is converted
     wait_next();  // chunk ch-1 done
     if (!ok) break;
     issue1(ch, ch & 1);
@@ -449,6 +552,16 @@ __global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args 
     // more bounded wait before tensor memory is released.
     mbar_wait(mbar, waited & 1);
   }
+  if constexpr (kTMA) {
+    // Copies still in flight after a failed wait land in this CTA's shared
+    // memory: wait for them (bounded) before the CTA exits.
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+      while (raw_done[b] < raw_issued[b]) {
+        mbar_wait(mraw + 8 * b, raw_done[b] & 1);
+        ++raw_done[b];
+      }
+  }
   __syncthreads();
   if (tid < 32) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -457,6 +570,51 @@ __global__ void __launch_bounds__(kUThreads, 1) split3_update_kernel(Bf16x3Args 
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link
+// against the driver library); null if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of a column-major FP32 matrix (rows x cols, leading dimension
+// ld elements) with boxes of box_rows x box_cols; reads past the matrix
+// return zeros.
+static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols, int64_t ld, uint32_t box_rows,
+                     uint32_t box_cols) {
+  const EncodeTiledFn f = encode_tiled();
+  if (!f) return false;
+  const cuuint64_t gdim[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  const cuuint64_t gstride[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {box_rows, box_cols};
+  const cuuint32_t estride[2] = {1, 1};
+  return f(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstride, box, estride,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool kTF32, bool kTMA>
+static cudaError_t launch_split3(const Bf16x3Args& a, const CUtensorMap& tmC, const CUtensorMap& tmY, dim3 grid,
+                                 cudaStream_t s) {
+  constexpr uint32_t smem = Split3<kTF32>::SmemBytes;
+  cudaError_t e = cudaFuncSetAttribute(split3_update_kernel<kTF32, kTMA>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  split3_update_kernel<kTF32, kTMA><<<grid, kUThreads, smem, s>>>(a, tmC, tmY);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_leaf_update_split3(const LeafApplyArgs<float>& la, bool tf32, int* status, cudaStream_t s) {
   if (la.nleaves <= 0 || la.k <= 0 || la.n <= 0) return cudaSuccess;
@@ -480,18 +638,20 @@ cudaError_t launch_leaf_update_split3(const LeafApplyArgs<float>& la, bool tf32,
   const int64_t kchunks = (la.k + kUN - 1) / kUN;
   if (kchunks > 65535 || la.nleaves > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   dim3 grid((unsigned)la.nleaves, (unsigned)kchunks);
-  if (tf32) {
-    constexpr uint32_t smem = Split3<true>::SmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(split3_update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    split3_update_kernel<true><<<grid, kUThreads, smem, s>>>(a);
-  } else {
-    constexpr uint32_t smem = Split3<false>::SmemBytes;
-    cudaError_t e = cudaFuncSetAttribute(split3_update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    split3_update_kernel<false><<<grid, kUThreads, smem, s>>>(a);
-  }
-  return cudaGetLastError();
+  // The copy engine path needs 16-byte aligned bases and leading dimensions
+  // and row coordinates (leaf starts, chunk starts) that are multiples of 4:
+  // exactly the conditions of the 16-byte thread loads (a.vec).  Rows stay
+  // below 2^31 so that the signed copy coordinates hold them.
+  CUtensorMap tmC, tmY;
+  std::memset(&tmC, 0, sizeof(tmC));
+  std::memset(&tmY, 0, sizeof(tmY));
+  const uint32_t chunk = tf32 ? Split3<true>::CHUNK : Split3<false>::CHUNK;
+  const bool tma = a.vec && la.m < (int64_t(1) << 31) && la.k < (int64_t(1) << 31) &&
+                   make_map(&tmC, la.C, la.m, la.k, la.ldc, chunk, kUN) &&
+                   make_map(&tmY, la.Y, la.m, la.n, la.ldy, chunk, kUNp);
+  if (tf32)
+    return tma ? launch_split3<true, true>(a, tmC, tmY, grid, s) : launch_split3<true, false>(a, tmC, tmY, grid, s);
+  return tma ? launch_split3<false, true>(a, tmC, tmY, grid, s) : launch_split3<false, false>(a, tmC, tmY, grid, s);
 }
 
 }  // namespace tsqr
