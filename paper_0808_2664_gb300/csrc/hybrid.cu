@@ -32,8 +32,9 @@ int leaf_factor_threads(int n, int ld, size_t elem);
 
 namespace {
 
+// FP32 chains, like FP32 leaves, keep two or more CTAs per SM (64 registers).
 template <typename T, int NT, int NMAX>
-__global__ void __launch_bounds__(NT) chain_factor_kernel(ChainFactorArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1) chain_factor_kernel(ChainFactorArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t nn = (int64_t)a.n * a.n;
   for (int64_t chain = blockIdx.x; chain < a.nchains; chain += gridDim.x) {

@@ -99,8 +99,8 @@ __device__ __forceinline__ int leaf_groups(int threads, int rows) {
 //       ready for the next step's reflector.
 // Three barriers per column among these warps; the bulk of the arithmetic
 // (update and dot) is one pass over the trailing block.  A separate group
-// of warps takes the products for T's Z = Y^T Y column by column as the
-// tails become final, off those barriers (see the loop below).
+// of warps takes the products for T's Z = Y^T Y as the tails become final,
+// off those barriers (see the loop below).
 //
 // Stacked form (kStacked, one step of the flat tree of Section 2.1): the
 // tile is [Rtop; A_i], the n x n upper-triangular R of the previous step
@@ -130,8 +130,13 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   T* Wt = Tm + (size_t)n * t_ld(n);    // doubling workspace
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  // Z warps (NT/128 when T is wanted): column pairs in FP64, 4 x 4 column
+  // blocks in FP32 (see the loop below).
+  constexpr bool kZPairs = kWantT && sizeof(T) == 8;
+  constexpr bool kZTiles = kWantT && sizeof(T) == 4;
   constexpr int kZWarps = kWantT ? leaf_z_warps(NT) : 0;
   constexpr int kUWarps = NT / 32 - 1 - kZWarps;
+  static_assert(32 * kUWarps <= leaf_part_entries(NT), "update partial dots exceed their slots");
   constexpr int kMThreads = 32 * (1 + kUWarps), kZThreads = 32 * kZWarps;
   constexpr int kS2Warps = 1 + kUWarps < 4 ? 1 + kUWarps : 4;  // warps of the single-column phase S2
 
@@ -214,10 +219,13 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   // the dots behind Z = strictly-upper(Y^T Y), needed for T:
   //   Z(p, q) = u_p^T u_q = s_p (a_p(q) + s_q a_p(q+1:)^T a_q(q+1:)),  p < q,
   // the unscaled dot d(p, q) = a_p(q+1:)^T a_q(q+1:) as soon as M reports
-  // column q's tail final, in pairs (p, p+1) per work item, with its own
-  // barrier; d goes to Tg and is turned into Z after the loop.  Z's work
-  // (about a third of the products) thus fills the FP64 pipe while M waits
-  // in its serial per-column steps.
+  // the tails final: in FP64, column q's dots in pairs (p, p+1) per work
+  // item with the group's own barrier, so that Z's work (about a third of
+  // the products) fills the FP64 pipe while M waits in its serial
+  // per-column steps; in FP32, whole 4 x 4 blocks of d per warp once a
+  // block of four columns is final (half a load per product instead of one
+  // and a half, less shared-memory traffic beside the latency-bound loop).
+  // d goes to Tg and is turned into Z after the loop.
   if (tid == 0) *zready = 0;
   __syncthreads();
   if (warp <= kUWarps) {
@@ -273,6 +281,26 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
               cc[k] = fma(-cs, up[k], cc[k]);
               i += rg;
             }
+            // Four rows per pass, all loads issued before the stores (the
+            // stores may alias later loads as far as the compiler knows);
+            // rows alternate between s0 and s1 as in the two-row tail.
+            for (; i + 3 * rg < hl; i += 4 * rg) {
+              T uv[4], av[4], xv[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                uv[u] = up[i + u * rg];
+                av[u] = cc[i + u * rg];
+                xv[u] = colk[i + u * rg];
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) av[u] = fma(-cs, uv[u], av[u]);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) cc[i + u * rg] = av[u];
+              s0 = fma(xv[0], av[0], s0);
+              s1 = fma(xv[1], av[1], s1);
+              s0 = fma(xv[2], av[2], s0);
+              s1 = fma(xv[3], av[3], s1);
+            }
             for (; i + rg < hl; i += 2 * rg) {
               const T a0 = fma(-cs, up[i], cc[i]);
               const T a1 = fma(-cs, up[i + rg], cc[i + rg]);
@@ -327,7 +355,7 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
         *zready = k + 1;  // column k+1's tail is final
       }
     }
-  } else if constexpr (kWantT) {
+  } else if constexpr (kZPairs) {
     const int ztid = tid - kMThreads;
     bool wait_ok = true;
     for (int q = 1; q < n; ++q) {
@@ -380,6 +408,94 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
         Tg[2 * t + q * n] = d1;
         if (2 * t + 1 < q) Tg[2 * t + 1 + q * n] = d2;
       }
+    }
+  } else if constexpr (kZTiles) {
+    // d = L^T L with L(r, c) = a_c(r) for r > c (the unscaled tails), p < q.
+    // Z warp zw takes tiles t = zw, zw + kZWarps, ... in block order (block
+    // Q holds t = Q(Q+1)/2 + P, P = 0..Q: columns 4P.., 4Q..) once column
+    // min(4Q + 3, n - 1)'s tail is final.  Lane l sums rows r = 4Q + 1 + l
+    // (mod 32); the 16 sums are reduce-scattered over the warp, entry s
+    // ending in lanes 2s and 2s + 1.
+    const int zw = warp - 1 - kUWarps;
+    const int nb = (n + 3) / 4;
+    bool wait_ok = true;
+    int Q = 0, base = 0;
+    for (int t = zw; t < nb * (nb + 1) / 2; t += kZWarps) {
+      while (base + Q + 1 <= t) {
+        base += Q + 1;
+        ++Q;
+      }
+      const int P = t - base;
+      const int need = 4 * Q + 3 < n - 1 ? 4 * Q + 3 : n - 1;
+      if (lane == 0 && wait_ok) {
+        int spins = 0;
+        while (*zready < need) {
+          if (++spins > (1 << 22)) {  // the update warps stopped reporting: give up, flag it
+            atomicOr(status, kStatusTimeout);
+            wait_ok = false;
+            break;
+          }
+          __nanosleep(64);
+        }
+        __threadfence_block();
+      }
+      __syncwarp();
+      int pc[4], qc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        pc[i] = (4 * P + i < n ? 4 * P + i : n - 1) * ld;
+        qc[i] = (4 * Q + i < n ? 4 * Q + i : n - 1) * ld;
+      }
+      T acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+      int r = 4 * Q + 1 + lane;
+      if (r < hl) {  // the only row of this lane that can lie in the block's own rows
+        T yp[4], yq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          yp[i] = S[pc[i] + r];
+          yq[i] = r > 4 * Q + i ? S[qc[i] + r] : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(yp[i], yq[j], acc[i][j]);
+        r += 32;
+      }
+#pragma unroll 2
+      for (; r < hl; r += 32) {
+        T yp[4], yq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          yp[i] = S[pc[i] + r];
+          yq[i] = S[qc[i] + r];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(yp[i], yq[j], acc[i][j]);
+      }
+      T v8[8], v4[4], v2[2];
+      bool up = lane & 16;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T lo = acc[u >> 2][u & 3], hi = acc[(u + 8) >> 2][(u + 8) & 3];
+        v8[u] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+      }
+      up = lane & 8;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v4[u] = (up ? v8[u + 4] : v8[u]) + __shfl_xor_sync(0xffffffffu, up ? v8[u] : v8[u + 4], 8);
+      up = lane & 4;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) v2[u] = (up ? v4[u + 2] : v4[u]) + __shfl_xor_sync(0xffffffffu, up ? v4[u] : v4[u + 2], 4);
+      up = lane & 2;
+      T v = (up ? v2[1] : v2[0]) + __shfl_xor_sync(0xffffffffu, up ? v2[0] : v2[1], 2);
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      const int sl = lane >> 1, p = 4 * P + (sl >> 2), q = 4 * Q + (sl & 3);
+      if (!(lane & 1) && p < q && q < n) Tg[p + q * n] = v;
     }
   }
   __syncthreads();

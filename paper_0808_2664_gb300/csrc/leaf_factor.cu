@@ -20,8 +20,11 @@
 namespace tsqr {
 namespace {
 
+// FP32 leaves are latency-bound and rely on two or more CTAs per SM to
+// overlap their column chains, so their register budget is held to 1024
+// threads' worth per SM (64 registers a thread).
 template <typename T, int NT, int NMAX>
-__global__ void __launch_bounds__(NT) leaf_factor_kernel(LeafFactorArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1) leaf_factor_kernel(LeafFactorArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int64_t nn = (int64_t)a.n * a.n;
   for (int64_t leaf = blockIdx.x; leaf < a.nleaves; leaf += gridDim.x) {
