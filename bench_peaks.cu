@@ -1,6 +1,7 @@
 // Throughput probes for the roofline denominators that MEASURED_PEAKS.json
 // does not hold: FP64 FMA, FP32 FMA and FP64 mma.sync m8n8k4 (DMMA) rates,
-// each from independent FMA chains over a full grid, timed with CUDA events.
+// each from independent FMA chains over a full grid, timed with CUDA events,
+// and DFMA and DMMA run side by side (whether they share the FP64 units).
 // The benchmark's FP64 roofline is derived from unit counts and clocks; these
 // rates show how close a plain FMA loop gets to it.  Build and run with
 // `python bench.py --peaks`, or:
@@ -50,6 +51,33 @@ __global__ void dmma(double* out, int iters) {
   double s = 0; for (int k = 0; k < 4; ++k) s += c[k][0] + c[k][1];
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// Half of each CTA's warps run FP64 FMA chains and half DMMA chains, each
+// half with the work it would do alone: if the two shared no units the pair
+// would finish in about half the time of either alone.
+__global__ void dfma_dmma(double* out, int iters_f, int iters_m, int fwarps) {
+  const int warp = threadIdx.x >> 5;
+  double s = 0;
+  if (warp < fwarps) {
+    double x[8];
+    for (int c = 0; c < 8; ++c) x[c] = threadIdx.x * 1e-3 + c;
+    for (int i = 0; i < iters_f; ++i) {
+      #pragma unroll
+      for (int c = 0; c < 8; ++c) x[c] = fma(x[c], 1.0000001, 1e-9);
+    }
+    for (int c = 0; c < 8; ++c) s += x[c];
+  } else {
+    double a = 1.0 + threadIdx.x * 1e-6, b = 0.5, c[4][2];
+    for (int k = 0; k < 4; ++k) { c[k][0] = 0; c[k][1] = 0; }
+    for (int i = 0; i < iters_m; ++i) {
+      #pragma unroll
+      for (int k = 0; k < 4; ++k)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                     : "+d"(c[k][0]), "+d"(c[k][1]) : "d"(a), "d"(b));
+    }
+    for (int k = 0; k < 4; ++k) s += c[k][0] + c[k][1];
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 int main() {
   int dev = 0; cudaDeviceProp p; CK(cudaGetDeviceProperties(&p, dev));
   printf("name=%s sms=%d cc=%d.%d smem/block optin=%zu l2=%d\n", p.name, p.multiProcessorCount, p.major, p.minor,
@@ -82,6 +110,15 @@ int main() {
     CK(cudaEventSynchronize(e1)); float ms; cudaEventElapsedTime(&ms, e0, e1);
     double fl = 2.0 * 8 * 8 * 4 * 4.0 * iters * (double)grid * (threads / 32);
     printf("dmma m8n8k4: bps=%d  %.3f ms  %.3f TFLOP/s\n", blocksPerSm, ms, fl / ms / 1e9);
+  }
+  for (int fw : {8, 0, 4}) {  // all DFMA, all DMMA, half and half (256 threads, one CTA per SM)
+    const int grid = sms, threads = 256, itf = 4096, itm = 1024;
+    dfma_dmma<<<grid, threads>>>(d, 16, 4, fw); CK(cudaDeviceSynchronize());
+    cudaEventRecord(e0); dfma_dmma<<<grid, threads>>>(d, itf, itm, fw); cudaEventRecord(e1);
+    CK(cudaEventSynchronize(e1)); float ms; cudaEventElapsedTime(&ms, e0, e1);
+    const double ff = 2.0 * 8 * itf * 32.0 * fw * grid, fm = 512.0 * 4 * itm * (8 - fw) * (double)grid;
+    printf("dfma warps %d + dmma warps %d: %.3f ms  %.3f + %.3f = %.3f TFLOP/s\n", fw, 8 - fw, ms, ff / ms / 1e9,
+           fm / ms / 1e9, (ff + fm) / ms / 1e9);
   }
   CK(cudaFree(d));
   return 0;
