@@ -1,7 +1,8 @@
 // Throughput probes for the roofline denominators that MEASURED_PEAKS.json
 // does not hold: FP64 FMA, FP32 FMA and FP64 mma.sync m8n8k4 (DMMA) rates,
 // each from independent FMA chains over a full grid, timed with CUDA events,
-// and DFMA and DMMA run side by side (whether they share the FP64 units).
+// DFMA and DMMA run side by side (whether they share the FP64 units), and a
+// dependent DFMA chain per warp with one or all lanes active.
 // The benchmark's FP64 roofline is derived from unit counts and clocks; these
 // rates show how close a plain FMA loop gets to it.  Build and run with
 // `python bench.py --peaks`, or:
@@ -78,6 +79,14 @@ __global__ void dfma_dmma(double* out, int iters_f, int iters_m, int fwarps) {
   }
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// A dependent FP64 FMA chain per warp with 1 or 32 active lanes: whether an
+// FP64 instruction's cost on its SM sub-partition depends on its lanes.
+__global__ void dfma_lanes(double* out, int iters, int lanes) {
+  double x = threadIdx.x * 1e-3;
+  if ((int)(threadIdx.x & 31) < lanes)
+    for (int i = 0; i < iters; ++i) x = fma(x, 1.0000001, 1e-9);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
 int main() {
   int dev = 0; cudaDeviceProp p; CK(cudaGetDeviceProperties(&p, dev));
   printf("name=%s sms=%d cc=%d.%d smem/block optin=%zu l2=%d\n", p.name, p.multiProcessorCount, p.major, p.minor,
@@ -119,6 +128,16 @@ int main() {
     const double ff = 2.0 * 8 * itf * 32.0 * fw * grid, fm = 512.0 * 4 * itm * (8 - fw) * (double)grid;
     printf("dfma warps %d + dmma warps %d: %.3f ms  %.3f + %.3f = %.3f TFLOP/s\n", fw, 8 - fw, ms, ff / ms / 1e9,
            fm / ms / 1e9, (ff + fm) / ms / 1e9);
+  }
+  for (int warps : {4, 8, 16}) {  // warps per SM (one CTA per SM), one dependent chain each
+    for (int lanes : {1, 32}) {
+      const int grid = sms, threads = 32 * warps, iters = 4096;
+      dfma_lanes<<<grid, threads>>>(d, 16, lanes); CK(cudaDeviceSynchronize());
+      cudaEventRecord(e0); dfma_lanes<<<grid, threads>>>(d, iters, lanes); cudaEventRecord(e1);
+      CK(cudaEventSynchronize(e1)); float ms; cudaEventElapsedTime(&ms, e0, e1);
+      printf("dfma chain: %2d warps/SM, %2d active lanes: %.3f ms, %.1f ns per dependent step\n", warps, lanes, ms,
+             ms * 1e6 / iters);
+    }
   }
   CK(cudaFree(d));
   return 0;
