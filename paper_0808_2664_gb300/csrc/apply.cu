@@ -233,12 +233,18 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
     const int r = rb + i;
     if (r < hl) {
       const int pmax = min(n, r + 1);  // Y(r, p) = 0 for p > r
+      const bool fresh = mode == kApplyForm && r >= n;  // rows below X start from zero
+      T* row = Cg + r;
+      // Each column's C entry is read before the previous column's store
+      // (the compiler cannot tell the two addresses apart), so its latency
+      // overlaps that column's dot product.
+      T old = (cg < kc && !fresh) ? row[(int64_t)cg * a.ldc] : T(0);
       for (int c = cg; c < kc; c += CG) {
+        const T next = (c + CG < kc && !fresh) ? row[(int64_t)(c + CG) * a.ldc] : T(0);
         T s = T(0);
         for (int p = 0; p < pmax; ++p) s = fma(Ys[i * ly + p], Ws[p * KC + c], s);
-        T* dst = Cg + r + (int64_t)c * a.ldc;
-        const T old = (mode == kApplyForm && r >= n) ? T(0) : *dst;
-        *dst = old - s;
+        row[(int64_t)c * a.ldc] = old - s;
+        old = next;
       }
     }
   }

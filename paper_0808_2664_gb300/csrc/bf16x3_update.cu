@@ -536,10 +536,19 @@ __global__ void __launch_bounds__(kUThreads, 1)
         float d[16];
         tmem_ld16(d2 + ((uint32_t)(quarter * 32) << 16) + c0, d);
         if (row < hl) {
+          // All sixteen loads before any store: the compiler cannot tell
+          // that the columns' addresses differ, and would otherwise wait
+          // out one read-modify-write of C before the next.
+          float cv[16];
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int c = c0 + e;
-            if (c < kc) Cg[row + (int64_t)c * a.ldc] -= d[e];
+            cv[e] = c < kc ? Cg[row + (int64_t)c * a.ldc] : 0.f;
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int c = c0 + e;
+            if (c < kc) Cg[row + (int64_t)c * a.ldc] = cv[e] - d[e];
           }
         }
       }
