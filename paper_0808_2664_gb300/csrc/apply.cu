@@ -15,6 +15,24 @@
 namespace tsqr {
 namespace {
 
+// Element loop idx = tid, tid + NT, ... < count doing st(idx, ld(idx)),
+// with four loads in flight per thread before their stores: a store through
+// a pointer the compiler cannot tell apart from the next load's would
+// otherwise make every load wait out the one before.
+template <int NT, class Ld, class St>
+__device__ __forceinline__ void copy4(int tid, int count, Ld ld, St st) {
+  int idx = tid;
+  for (; idx + 3 * NT < count; idx += 4 * NT) {
+    const auto v0 = ld(idx), v1 = ld(idx + NT), v2 = ld(idx + 2 * NT), v3 = ld(idx + 3 * NT);
+    st(idx, v0);
+    st(idx + NT, v1);
+    st(idx + 2 * NT, v2);
+    st(idx + 3 * NT, v3);
+  }
+  for (; idx < count; idx += NT) st(idx, ld(idx));
+}
+
+
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 // ---------------------------------------------------------------- leaves --
@@ -100,12 +118,15 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
     }
   };
   auto direct_y = [&](int rb, int rows) {
-    for (int idx = tid; idx < RB * n; idx += NT) {
-      const int i = idx % RB, p = idx / RB, r = rb + i;
-      T v = T(0);
-      if (r < rows) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
-      Ys[i * ly + p] = v;
-    }
+    copy4<NT>(
+        tid, RB * n,
+        [&](int idx) {
+          const int i = idx % RB, p = idx / RB, r = rb + i;
+          T v = T(0);
+          if (r < rows) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
+          return v;
+        },
+        [&](int idx, T v) { Ys[(idx % RB) * ly + idx / RB] = v; });
   };
   auto stage_y = [&]() {
 #pragma unroll
@@ -140,10 +161,13 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
       stage_c();
     } else {
       direct_y(rb, rows1);
-      for (int idx = tid; idx < RB * KC; idx += NT) {
-        const int i = idx % RB, c = idx / RB, r = rb + i;
-        Cs[i * lc + c] = (r < rows1 && c < kc) ? Cg[r + (int64_t)c * a.ldc] : T(0);
-      }
+      copy4<NT>(
+          tid, RB * KC,
+          [&](int idx) {
+            const int i = idx % RB, c = idx / RB, r = rb + i;
+            return (r < rows1 && c < kc) ? Cg[r + (int64_t)c * a.ldc] : T(0);
+          },
+          [&](int idx, T v) { Cs[(idx % RB) * lc + idx / RB] = v; });
     }
     __syncthreads();
     if (kPrefetch && rb + RB < rows1) {
