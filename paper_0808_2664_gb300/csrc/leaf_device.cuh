@@ -35,7 +35,8 @@ __host__ __device__ constexpr int leaf_part_entries(int nt) { return leaf_upart(
 // Shared-memory bytes for a leaf of up to ld rows with NT threads: the tile
 // region, the partial dots, two per-column coefficient vectors, and FP64
 // per-column scalars (tau, reflector scale, scaling exponent) plus 128
-// per-lane partial norms and the Z group's progress word.
+// per-lane partial norms, the Z group's progress word and the warp-role
+// rotation.
 __host__ __device__ inline size_t leaf_smem_bytes(int n, int ld, size_t elem, int nt) {
   return leaf_tile_region(n, ld, elem) + leaf_align_up(elem * (size_t)leaf_part_entries(nt), 8) +
          2 * leaf_align_up(elem * (size_t)n, 8) + sizeof(double) * (3 * (size_t)n + 128 + 2);
@@ -128,7 +129,22 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   volatile int* zready = reinterpret_cast<volatile int*>(wsum + 128);  // columns whose tails are final
   T* Tm = reinterpret_cast<T*>(smem);  // n x n (leading dimension t_ld(n)), after write-back
   T* Wt = Tm + (size_t)n * t_ld(n);    // doubling workspace
-  const int tid = threadIdx.x;
+  // Warp roles rotate by the CTA's position on its SM: the hardware warp
+  // slot of thread 0 (a placement hint only) picks a rotation that is
+  // shared through shared memory, so the roles stay consistent within the
+  // CTA.  Co-resident CTAs then put their reflector warps (and the other
+  // single-warp FP64 steps) on different SM sub-partitions, whose FP64 unit
+  // an FP64 instruction holds whatever its active lanes.
+  {
+    int* rot_s = reinterpret_cast<int*>(wsum + 129);
+    if (threadIdx.x == 0) {
+      unsigned ws;
+      asm volatile("mov.u32 %0, %%warpid;" : "=r"(ws));
+      *rot_s = (int)((ws / (NT / 32)) & 3u);
+    }
+    __syncthreads();
+  }
+  const int tid = (int)(threadIdx.x + 32u * (unsigned)*reinterpret_cast<volatile int*>(wsum + 129)) % NT;
   const int lane = tid & 31, warp = tid >> 5;
   // Z warps (NT/128 when T is wanted): column pairs in FP64, 4 x 4 column
   // blocks in FP32 (see the loop below).
