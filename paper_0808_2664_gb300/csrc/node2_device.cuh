@@ -73,6 +73,7 @@ template <typename T, int NT, int G, int Q, bool kBuildT = true>
 __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64_t nodes, int64_t node0, int n,
                                    T* Rout, T* Yout, T* Tout, T* tauout, int* status, unsigned char* smem) {
   static_assert(NT / 32 >= 2 * G + 2, "need a reflector warp, two S warps per node and a Z warp");
+  static_assert(G < 31, "ssq[31] holds the warp-role rotation");
   const int pk = node2_packed(n);
   T* D = reinterpret_cast<T*>(smem);
   unsigned char* aux = smem + node2_region_bytes(n, G, sizeof(T), Q);
@@ -83,7 +84,20 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
   double* sc_s = tau_s + G * n;                         // G n: reflector scales
   int* cexp = reinterpret_cast<int*>(sc_s + G * n);     // G n: column exponents (G n doubles reserved)
   double* ssq = sc_s + 2 * G * n;                       // G: squared tail norms
-  const int tid = threadIdx.x;
+  // Warp roles rotate by the CTA's slot on its SM (thread 0's hardware warp
+  // slot, a placement hint shared through shared memory; ssq + 31 is a
+  // spare slot), as in the leaf: co-resident CTAs put their single-warp
+  // FP64 steps on different sub-partitions.
+  {
+    int* rot_s = reinterpret_cast<int*>(ssq + 31);
+    if (threadIdx.x == 0) {
+      unsigned ws;
+      asm volatile("mov.u32 %0, %%warpid;" : "=r"(ws));
+      *rot_s = (int)((ws / (NT / 32)) & 3u);
+    }
+    __syncthreads();
+  }
+  const int tid = (int)(threadIdx.x + 32u * (unsigned)*reinterpret_cast<volatile int*>(ssq + 31)) % NT;
   const int lane = tid & 31, warp = tid >> 5;
   constexpr int kPWarps = NT / 32 - 1;
   const int64_t nn = (int64_t)n * n;
