@@ -688,10 +688,10 @@ def ours(args, world, rank, local):
     peak = FP64_PEAK_GFLOPS / 1e3
     kernel_name = {"leaf_factor": "leaf_factor_kernel<double>", "leaf_apply": "leaf_apply_kernel<double> (form)"}[dom]
     # DRAM traffic of the leaf-factor launch: one ncu capture of this kernel (n = 64, h = 416) at
-    # m = 524,288 read + wrote 567.1 MB; A, Y and the per-leaf R/T scale with the rows.
+    # m = 524,288 read + wrote 567.3 MB; A, Y and the per-leaf R/T scale with the rows.
     traffic = None
     if dom == "leaf_factor" and n == 64 and h == 416:
-        traffic = 567.1e6 / 524288 * m
+        traffic = 567.3e6 / 524288 * m
     roofline = {"bound": "alu", "kernel": kernel_name, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (probe measured 1.19-1.26)",
