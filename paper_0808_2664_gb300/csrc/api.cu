@@ -101,6 +101,7 @@ struct caqr_q_s {
   // trailing matrix is updated on the caller's stream.
   cudaStream_t side = nullptr;
   std::vector<cudaEvent_t> ev_left, ev_fact;
+  std::vector<cudaEvent_t> ev_leaf;  // a panel's leaf factors are in (its tree may still run)
   // The FP64 trailing update of a wide panel is issued as two column halves
   // on the caller's stream and on `upd2`, so that one half's latency-bound
   // tree levels overlap the other half's leaf blocks.
@@ -352,7 +353,8 @@ ChainApplyArgs<T> chain_apply_args(const tsqr_q_s* q, int mode, int64_t k, T* C,
 }
 
 template <typename T>
-cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
+cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool zero_lower, cudaStream_t s,
+                       cudaEvent_t ev_leaves = nullptr) {
   StageTimer t0(q, TSQR_STAGE_LEAF_FACTOR, s);
   cudaError_t e;
   if (q->hybrid) {
@@ -376,6 +378,9 @@ cudaError_t run_factor(tsqr_q_s* q, T* A, int64_t lda, T* R, int64_t ldr, bool z
   }
   if (e != cudaSuccess) return e;
   t0.stop(1);
+  // The leaf factors (Y, T per leaf) are complete here: a caller may start
+  // leaf-level products on another stream while the tree is factored.
+  if (ev_leaves && (e = cudaEventRecord(ev_leaves, s)) != cudaSuccess) return e;
   return run_tree_factor(q, R, ldr, zero_lower, s);
 }
 
@@ -429,7 +434,7 @@ cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s, 
 
 template <typename T>
 cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc, cudaStream_t s, const T* X = nullptr,
-                      int64_t ldx = 0) {
+                      int64_t ldx = 0, cudaEvent_t tree_ready = nullptr) {
   cudaError_t e = cudaSuccess;
   LeafApplyArgs<T> la = leaf_apply_args(q, k, C, ldc, 0, q->nleaves);
   auto node = [&](int l, int md) {
@@ -469,6 +474,9 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
   };
   if (mode == kApplyQT) {
     if ((e = leaf(kApplyQT)) != cudaSuccess) return e;
+    // The tree stage needs the node factors: a caller that started this
+    // product before the tree was factored passes the tree's event.
+    if (tree_ready && (e = cudaStreamWaitEvent(s, tree_ready, 0)) != cudaSuccess) return e;
     StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
     for (int l = 1; l <= q->levels; ++l)
       if ((e = node(l, kApplyQT)) != cudaSuccess) return e;
@@ -625,12 +633,13 @@ int create_handle(int64_t m, int64_t n, int32_t prec, const tsqr_opts_t* opts, t
   return TSQR_OK;
 }
 
-int refactor(tsqr_q_s* q, void* A, int64_t lda, void* R, int64_t ldr, bool zero_lower, cudaStream_t s) {
+int refactor(tsqr_q_s* q, void* A, int64_t lda, void* R, int64_t ldr, bool zero_lower, cudaStream_t s,
+             cudaEvent_t ev_leaves = nullptr) {
   cudaError_t e;
   if (q->prec == TSQR_PREC_FP64)
-    e = run_factor<double>(q, (double*)A, lda, (double*)R, ldr, zero_lower, s);
+    e = run_factor<double>(q, (double*)A, lda, (double*)R, ldr, zero_lower, s, ev_leaves);
   else
-    e = run_factor<float>(q, (float*)A, lda, (float*)R, ldr, zero_lower, s);
+    e = run_factor<float>(q, (float*)A, lda, (float*)R, ldr, zero_lower, s, ev_leaves);
   if (e != cudaSuccess) return cuda_err(e);
   q->A = A;
   q->lda = lda;
@@ -690,14 +699,15 @@ int factor_common(int64_t m, int64_t n, T* A, int64_t lda, T* R, int64_t ldr, co
   return TSQR_OK;
 }
 
-int apply_common(tsqr_q_s* q, int mode, int64_t k, void* C, int64_t ldc, cudaStream_t s) {
+int apply_common(tsqr_q_s* q, int mode, int64_t k, void* C, int64_t ldc, cudaStream_t s,
+                 cudaEvent_t tree_ready = nullptr) {
   if (!valid(q) || !q->factored) return TSQR_ERR_HANDLE;
   if (k < 0) return -2;
   if (k == 0) return TSQR_OK;
   if (!C) return -3;
   if (ldc < q->m) return -4;
-  cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, mode, k, (double*)C, ldc, s)
-                                            : run_apply<float>(q, mode, k, (float*)C, ldc, s);
+  cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, mode, k, (double*)C, ldc, s, nullptr, 0, tree_ready)
+                                            : run_apply<float>(q, mode, k, (float*)C, ldc, s, nullptr, 0, tree_ready);
   return cuda_err(e);
 }
 
@@ -995,11 +1005,13 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
   if (rc == TSQR_OK && cudaStreamCreateWithFlags(&c->upd2, cudaStreamNonBlocking) != cudaSuccess) rc = TSQR_ERR_CUDA;
   c->ev_left.assign(c->panels.size(), nullptr);
   c->ev_fact.assign(c->panels.size(), nullptr);
+  c->ev_leaf.assign(c->panels.size(), nullptr);
   c->ev_fork.assign(c->panels.size(), nullptr);
   c->ev_join.assign(c->panels.size(), nullptr);
   for (size_t j = 0; j < c->panels.size() && rc == TSQR_OK; ++j) {
     if (cudaEventCreateWithFlags(&c->ev_left[j], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fact[j], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_leaf[j], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork[j], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join[j], cudaEventDisableTiming) != cudaSuccess)
       rc = TSQR_ERR_CUDA;
@@ -1022,7 +1034,11 @@ static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
   // loop; the overlap is this implementation's): panel j+1's columns get
   // (Q_j D_j)^T first, then panel j+1 is factored on the side stream while
   // the remaining trailing columns are updated on the caller's stream.  The
-  // two touch disjoint columns of A.
+  // two touch disjoint columns of A.  The leaf stage of panel j+1's update
+  // needs only panel j's leaf factors, so (except under stage timing, whose
+  // stage times must not overlap) it starts when those are in and runs
+  // beside panel j's tree factorisation; its tree stage waits for the tree.
+  const bool overlap = !c->timing;
   const size_t np = c->panels.size();
   const size_t es = c->es;
   auto at = [&](int64_t i, int64_t j) -> void* { return (unsigned char*)A + (size_t)(i + j * lda) * es; };
@@ -1035,12 +1051,12 @@ static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
     const int64_t j1 = j0 + p->n;          // first trailing column
     if (j + 1 == np) break;
     tsqr_q_s* nx = c->panels[j + 1];
-    rc = apply_common(p, kApplyQT, nx->n, at(j0, j1), lda, s);
+    rc = apply_common(p, kApplyQT, nx->n, at(j0, j1), lda, s, overlap && j > 0 ? c->ev_fact[j] : nullptr);
     if (rc != TSQR_OK) return rc;
     if (cudaEventRecord(c->ev_left[j], s) != cudaSuccess) return TSQR_ERR_CUDA;
     if (cudaStreamWaitEvent(c->side, c->ev_left[j], 0) != cudaSuccess) return TSQR_ERR_CUDA;
     void* P = at(j1, j1);
-    rc = refactor(nx, P, lda, P, lda, false, c->side);
+    rc = refactor(nx, P, lda, P, lda, false, c->side, overlap ? c->ev_leaf[j + 1] : nullptr);
     if (rc != TSQR_OK) return rc;
     if (cudaEventRecord(c->ev_fact[j + 1], c->side) != cudaSuccess) return TSQR_ERR_CUDA;
     const int64_t kt = c->n - j1 - nx->n;
@@ -1064,8 +1080,14 @@ static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
       rc = apply_common(p, kApplyQT, kt1, at(j0, j1 + nx->n), lda, s);
       if (rc != TSQR_OK) return rc;
     }
-    if (cudaStreamWaitEvent(s, c->ev_fact[j + 1], 0) != cudaSuccess) return TSQR_ERR_CUDA;
+    // Panel j+1's leaf factors (overlap) or its whole factorisation: the
+    // next iteration's first product needs the former, its tree stage
+    // waits for ev_fact[j + 1] itself.
+    if (cudaStreamWaitEvent(s, overlap ? c->ev_leaf[j + 1] : c->ev_fact[j + 1], 0) != cudaSuccess)
+      return TSQR_ERR_CUDA;
   }
+  // The last panel's tree (its R rows) before the caller's stream goes on.
+  if (overlap && np > 1 && cudaStreamWaitEvent(s, c->ev_fact[np - 1], 0) != cudaSuccess) return TSQR_ERR_CUDA;
   if (joined >= 0 && cudaStreamWaitEvent(s, c->ev_join[joined], 0) != cudaSuccess) return TSQR_ERR_CUDA;
   return TSQR_OK;
 }
@@ -1252,6 +1274,8 @@ int caqr_q_destroy(caqr_q_t q) {
   for (auto e : q->ev_left)
     if (e) cudaEventDestroy(e);
   for (auto e : q->ev_fact)
+    if (e) cudaEventDestroy(e);
+  for (auto e : q->ev_leaf)
     if (e) cudaEventDestroy(e);
   for (auto e : q->ev_fork)
     if (e) cudaEventDestroy(e);
