@@ -85,6 +85,10 @@ struct tsqr_q_s {
   cudaStream_t copy = nullptr;
   std::vector<cudaEvent_t> ev_in, ev_out;
   cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+  // CAQR panels: one event per tree level, recorded as the level's factors
+  // are written, and one after the sign fix, so that another stream's Q^T
+  // product can take each level as soon as it is factored (empty: none).
+  std::vector<cudaEvent_t> ev_level;
 };
 
 struct caqr_q_s {
@@ -402,8 +406,10 @@ cudaError_t run_tree_factor(tsqr_q_s* q, T* R, int64_t ldr, bool zero_lower, cud
     na.status = q->status;
     e = launch_node_factor(na, s);
     if (e != cudaSuccess) return e;
+    if (!q->ev_level.empty() && (e = cudaEventRecord(q->ev_level[l - 1], s)) != cudaSuccess) return e;
   }
   e = launch_sign_fix((const T*)root_r(q), (int)q->n, (T*)q->d, R, ldr, zero_lower, s);
+  if (e == cudaSuccess && !q->ev_level.empty()) e = cudaEventRecord(q->ev_level[q->levels], s);
   if (e == cudaSuccess) t1.stop(q->levels + 1);
   return e;
 }
@@ -434,7 +440,7 @@ cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s, 
 
 template <typename T>
 cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc, cudaStream_t s, const T* X = nullptr,
-                      int64_t ldx = 0, cudaEvent_t tree_ready = nullptr) {
+                      int64_t ldx = 0, bool wait_tree = false) {
   cudaError_t e = cudaSuccess;
   LeafApplyArgs<T> la = leaf_apply_args(q, k, C, ldc, 0, q->nleaves);
   auto node = [&](int l, int md) {
@@ -474,12 +480,16 @@ cudaError_t run_apply(const tsqr_q_s* q, int mode, int64_t k, T* C, int64_t ldc,
   };
   if (mode == kApplyQT) {
     if ((e = leaf(kApplyQT)) != cudaSuccess) return e;
-    // The tree stage needs the node factors: a caller that started this
-    // product before the tree was factored passes the tree's event.
-    if (tree_ready && (e = cudaStreamWaitEvent(s, tree_ready, 0)) != cudaSuccess) return e;
+    // Each tree level needs its node factors: a caller that started this
+    // product while the tree was still being factored on another stream
+    // (wait_tree) waits for each level's event, then for the sign fix's.
+    const bool per_level = wait_tree && (int)q->ev_level.size() == q->levels + 1;
     StageTimer t(q, TSQR_STAGE_TREE_APPLY, s);
-    for (int l = 1; l <= q->levels; ++l)
+    for (int l = 1; l <= q->levels; ++l) {
+      if (per_level && (e = cudaStreamWaitEvent(s, q->ev_level[l - 1], 0)) != cudaSuccess) return e;
       if ((e = node(l, kApplyQT)) != cudaSuccess) return e;
+    }
+    if (per_level && (e = cudaStreamWaitEvent(s, q->ev_level[q->levels], 0)) != cudaSuccess) return e;
     e = launch_scale_rows(C, ldc, (int)q->n, k, (const T*)q->d, s);
     if (e == cudaSuccess) t.stop(q->levels + 1);
     return e;
@@ -657,6 +667,8 @@ int destroy_handle(tsqr_q_s* q) {
     cudaEventDestroy(q->ev_in[i]);
     cudaEventDestroy(q->ev_out[i]);
   }
+  for (auto e : q->ev_level)
+    if (e) cudaEventDestroy(e);
   if (q->ev_start) cudaEventDestroy(q->ev_start);
   if (q->ev_done) cudaEventDestroy(q->ev_done);
   if (q->copy) cudaStreamDestroy(q->copy);
@@ -700,14 +712,14 @@ int factor_common(int64_t m, int64_t n, T* A, int64_t lda, T* R, int64_t ldr, co
 }
 
 int apply_common(tsqr_q_s* q, int mode, int64_t k, void* C, int64_t ldc, cudaStream_t s,
-                 cudaEvent_t tree_ready = nullptr) {
+                 bool wait_tree = false) {
   if (!valid(q) || !q->factored) return TSQR_ERR_HANDLE;
   if (k < 0) return -2;
   if (k == 0) return TSQR_OK;
   if (!C) return -3;
   if (ldc < q->m) return -4;
-  cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, mode, k, (double*)C, ldc, s, nullptr, 0, tree_ready)
-                                            : run_apply<float>(q, mode, k, (float*)C, ldc, s, nullptr, 0, tree_ready);
+  cudaError_t e = q->prec == TSQR_PREC_FP64 ? run_apply<double>(q, mode, k, (double*)C, ldc, s, nullptr, 0, wait_tree)
+                                            : run_apply<float>(q, mode, k, (float*)C, ldc, s, nullptr, 0, wait_tree);
   return cuda_err(e);
 }
 
@@ -1015,6 +1027,10 @@ int caqr_q_create(int64_t m, int64_t n, int64_t b, int32_t update_precision, con
         cudaEventCreateWithFlags(&c->ev_fork[j], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join[j], cudaEventDisableTiming) != cudaSuccess)
       rc = TSQR_ERR_CUDA;
+    tsqr_q_s* p = c->panels[j];
+    p->ev_level.assign(p->levels + 1, nullptr);
+    for (auto& e : p->ev_level)
+      if (rc == TSQR_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) rc = TSQR_ERR_CUDA;
   }
   if (rc != TSQR_OK) {
     caqr_q_destroy(c);
@@ -1051,7 +1067,7 @@ static int caqr_issue(caqr_q_t c, void* A, int64_t lda, cudaStream_t s) {
     const int64_t j1 = j0 + p->n;          // first trailing column
     if (j + 1 == np) break;
     tsqr_q_s* nx = c->panels[j + 1];
-    rc = apply_common(p, kApplyQT, nx->n, at(j0, j1), lda, s, overlap && j > 0 ? c->ev_fact[j] : nullptr);
+    rc = apply_common(p, kApplyQT, nx->n, at(j0, j1), lda, s, overlap && j > 0);
     if (rc != TSQR_OK) return rc;
     if (cudaEventRecord(c->ev_left[j], s) != cudaSuccess) return TSQR_ERR_CUDA;
     if (cudaStreamWaitEvent(c->side, c->ev_left[j], 0) != cudaSuccess) return TSQR_ERR_CUDA;
