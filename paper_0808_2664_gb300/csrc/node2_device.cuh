@@ -73,7 +73,15 @@ template <typename T, int NT, int G, int Q, bool kBuildT = true>
 __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64_t nodes, int64_t node0, int n,
                                    T* Rout, T* Yout, T* Tout, T* tauout, int* status, unsigned char* smem) {
   static_assert(NT / 32 >= 2 * G + 2, "need a reflector warp, two S warps per node and a Z warp");
-  static_assert(G < 31, "ssq[31] holds the warp-role rotation");
+  // Next-column (S) warps per node: on the 512-thread CTAs of the narrow,
+  // latency-bound levels, one per lower triangle when the CTA has the warps
+  // (each on its own sub-partition: the FP64 squared norm of a triangle's
+  // column per warp); else one for all of them (wide levels, where three
+  // CTAs share an SM, lose to the extra warps' repeated coefficient work).
+  constexpr int kSW = (NT >= 512 && (NT / 32 - 2 - G) / G >= Q - 1) ? Q - 1 : 1;
+  constexpr int kS = G * kSW, kSC = kS + G;  // S warps 1..kS, coefficient warps kS+1..kSC
+  static_assert(NT / 32 >= kSC + 2, "need a reflector warp, the S and coefficient warps and a Z warp");
+  static_assert(kS < 31, "ssq[0..kS) holds the partial squared norms, ssq[31] the warp-role rotation");
   const int pk = node2_packed(n);
   T* D = reinterpret_cast<T*>(smem);
   unsigned char* aux = smem + node2_region_bytes(n, G, sizeof(T), Q);
@@ -83,7 +91,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
   double* tau_s = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(cscl) + leaf_align_up(sizeof(T) * G * n, 8));
   double* sc_s = tau_s + G * n;                         // G n: reflector scales
   int* cexp = reinterpret_cast<int*>(sc_s + G * n);     // G n: column exponents (G n doubles reserved)
-  double* ssq = sc_s + 2 * G * n;                       // G: squared tail norms
+  double* ssq = sc_s + 2 * G * n;                       // G kSW: partial squared tail norms
   // Warp roles rotate by the CTA's slot on its SM (thread 0's hardware warp
   // slot, a placement hint shared through shared memory; ssq + 31 is a
   // spare slot), as in the leaf: co-resident CTAs put their single-warp
@@ -160,12 +168,16 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
   }
   __syncthreads();
   if (tid < G) {
-    double x2 = 0.0;
-    for (int b = 1; b < Q; ++b) {
-      const double x = (double)col(tid, b, 0)[0];
-      x2 = fma(x, x, x2);
+    // Column 0's squared tail norm, as the S warps' partial sums: part s
+    // of node g over triangles b = 1 + s, 1 + s + kSW, ...
+    for (int sw = 0; sw < kSW; ++sw) {
+      double x2 = 0.0;
+      for (int b = 1 + sw; b < Q; b += kSW) {
+        const double x = (double)col(tid, b, 0)[0];
+        x2 = fma(x, x, x2);
+      }
+      ssq[tid * kSW + sw] = x2;
     }
-    ssq[tid] = x2;
   }
   __syncthreads();
 
@@ -190,8 +202,14 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
         const int g = lane;
         T* ck0 = col(g, 0, k);
         const double alpha = (double)ck0[k];
+        double ss = ssq[g * kSW];
+        for (int sw = 1; sw < kSW; ++sw) ss += ssq[g * kSW + sw];
+        // R_0(k-1, k): H_{k-1}'s unit entry on row k-1 of this column (the
+        // S warps all read that entry for their coefficient, so it is
+        // updated only now).
+        if (k > 0) ck0[k - 1] -= coef[g * n + k];
         Reflector r = make_reflector_fast(
-            alpha, ssq[g],
+            alpha, ss,
             [&]() { return scaled_norm((Q - 1) * (k + 1), [&](int v) { return (double)col(g, 1 + v / (k + 1), k)[v % (k + 1)]; }); },
             status);
         tau_s[g * n + k] = r.tau;
@@ -277,8 +295,8 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
     // 0..k+1).  Warp 1 + G + g forms the coefficients of node g's other
     // trailing columns (lanes over columns) at the same time; the remaining
     // warps take the Z entries of column k.
-    if (warp >= 1 && warp <= 2 * G && acols > 0) {
-      const int g = (warp - 1) % G;
+    if (warp >= 1 && warp <= kSC && acols > 0) {
+      const int g = warp <= kS ? (warp - 1) / kSW : warp - 1 - kS;
       const double tk = tau_s[g * n + k], sk = sc_s[g * n + k], ts = tk * sk;
       auto w_of = [&](int j) {
         const int sl = g * acols + j;
@@ -291,14 +309,13 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
         if (gg < rg) d0 += part[gg * ucols + sl];
         return fma(sk, (double)(d0 + d1), (double)col(g, 0, k + 1 + j)[k]);
       };
-      if (warp <= G) {
+      if (warp <= kS) {
+        const int sw = (warp - 1) % kSW;
         const double w = w_of(0);
         const T cf1 = (T)(tk * w), cs1 = (T)(ts * w);
-        __syncwarp();
-        if (lane == 0) col(g, 0, k + 1)[k] -= cf1;
+        if (sw == 0 && lane == 0) coef[g * n + k + 1] = cf1;  // row k of column k+1: next reflector step
         double ss = 0.0;
-#pragma unroll
-        for (int b = 1; b < Q; ++b) {
+        for (int b = 1 + sw; b < Q; b += kSW) {
           T* cc1 = col(g, b, k + 1);
           const T* ak = col(g, b, k);
           for (int i = lane; i <= k + 1; i += 32) {
@@ -312,7 +329,7 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0) ssq[g] = ss;
+        if (lane == 0) ssq[g * kSW + sw] = ss;
       } else {
         for (int j = 1 + lane; j < acols; j += 32) {
           const double w = w_of(j);
@@ -320,8 +337,8 @@ __device__ void node2_factor_group(const T* __restrict__ Rin, int64_t nin, int64
           cscl[g * n + k + 1 + j] = (T)(ts * w);
         }
       }
-    } else if (kBuildT && warp > 2 * G) {
-      for (int zs = tid - 32 * (2 * G + 1); zs < zcols; zs += NT - 32 * (2 * G + 1)) {
+    } else if (kBuildT && warp > kSC) {
+      for (int zs = tid - 32 * (kSC + 1); zs < zcols; zs += NT - 32 * (kSC + 1)) {
         const int np = npairs > 0 ? npairs : 1;
         const int g = zs / np, t = zs % np;
         T d1 = T(0), d2 = T(0);
