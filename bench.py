@@ -657,6 +657,14 @@ def ours(args, world, rank, local):
         rate, ms, dt, cores = oracle_rows_per_s(args.m, args.n, args.cpu_seconds)
         cpu = {"value": rate, "unit": "rows/s", "cores": cores, "kind": "oracle",
                "sample": f"{ms} x {args.n} rows (factor + thin Q) of the {args.m} x {args.n} workload, {dt:.1f} s"}
+        import oracle as _oracle
+        _oracle.set_num_threads(1)
+        try:
+            r1, ms1, dt1, _ = oracle_rows_per_s(args.m, args.n, args.cpu_seconds)
+        finally:
+            _oracle.set_num_threads(cores)
+        cpu["single_thread"] = {"value": r1, "unit": "rows/s", "cores": 1,
+                                "sample": f"{ms1} x {args.n} rows of the same workload, {dt1:.1f} s"}
 
     tq._lib.lib()
     if dist:

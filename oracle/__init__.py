@@ -80,6 +80,8 @@ def _load():
             lib.oracle_qr_backward.argtypes = [i64, i64, dp, dp, dp, dp, dp]
             lib.oracle_lstsq.argtypes = [i64, i64, dp, i64, i64, dp, i64, dp, i64, dp]
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_num_threads.restype = None
             for f in (lib.oracle_geqr2, lib.oracle_extract_r, lib.oracle_apply_qt, lib.oracle_apply_q,
                       lib.oracle_form_q, lib.oracle_larft, lib.oracle_qr, lib.oracle_qr_backward, lib.oracle_lstsq):
                 f.restype = None
@@ -213,3 +215,8 @@ def lstsq(A, B):
 def num_threads() -> int:
     """OpenMP threads the oracle uses (set OMP_NUM_THREADS before the first call)."""
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(nthreads: int) -> None:
+    """Sets the OpenMP threads of later oracle calls (timing on one core)."""
+    _load().oracle_set_num_threads(int(nthreads))

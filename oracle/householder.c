@@ -290,3 +290,13 @@ int oracle_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Sets the number of OpenMP threads for later calls (no effect without
+ * OpenMP); for timing the oracle on one core beside all of them. */
+void oracle_set_num_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+}
