@@ -244,7 +244,54 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
         if (p0 + x < n && c0 + y < KC) Ws[(p0 + x) * KC + c0 + y] = acc[t][x][y];
   }
 
-  // Phase 3: C <- C - Y W  (form: C <- [X; 0] - Y W).  Thread = (row, column group).
+  // Phase 3: C <- C - Y W  (form: C <- [X; 0] - Y W).
+  if constexpr (sizeof(T) == 4) {
+    // FP32: lane = row of the 32-row block, warp = 8 contiguous columns, all
+    // eight dot products at once (W read as two float4 per p, eight
+    // independent chains, the eight C entries read before any store); each
+    // dot runs over p in order as below, so the results are the same.
+    static_assert(RB == 32 && (NT / 32) * 8 == KC, "phase 3 layout: a warp per 8 columns of a 32-row block");
+    const int i = tid & 31, c0 = (tid >> 5) * 8;
+    if (kPrefetch) fetch_y(0, hl);
+    for (int rb = 0; rb < hl; rb += RB) {
+      __syncthreads();
+      if (kPrefetch) stage_y();
+      else direct_y(rb, hl);
+      __syncthreads();
+      if (kPrefetch && rb + RB < hl) fetch_y(rb + RB, hl);
+      const int r = rb + i;
+      if (r < hl && c0 < kc) {
+        const int pmax = min(n, r + 1);  // Y(r, p) = 0 for p > r
+        const bool fresh = mode == kApplyForm && r >= n;  // rows below X start from zero
+        T* row = Cg + r;
+        T old[8], acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          old[j] = (c0 + j < kc && !fresh) ? row[(int64_t)(c0 + j) * a.ldc] : T(0);
+          acc[j] = T(0);
+        }
+        const T* yr = Ys + i * ly;
+        for (int p = 0; p < pmax; ++p) {
+          const T y = yr[p];
+          const float4 w0 = *reinterpret_cast<const float4*>(Ws + p * KC + c0);
+          const float4 w1 = *reinterpret_cast<const float4*>(Ws + p * KC + c0 + 4);
+          acc[0] = fma(y, w0.x, acc[0]);
+          acc[1] = fma(y, w0.y, acc[1]);
+          acc[2] = fma(y, w0.z, acc[2]);
+          acc[3] = fma(y, w0.w, acc[3]);
+          acc[4] = fma(y, w1.x, acc[4]);
+          acc[5] = fma(y, w1.y, acc[5]);
+          acc[6] = fma(y, w1.z, acc[6]);
+          acc[7] = fma(y, w1.w, acc[7]);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (c0 + j < kc) row[(int64_t)(c0 + j) * a.ldc] = old[j] - acc[j];
+      }
+    }
+    return;
+  }
+  // FP64: thread = (row, column group).
   constexpr int CG = NT / RB;
   const int i = tid % RB, cg = tid / RB;
   if (kPrefetch) fetch_y(0, hl);
