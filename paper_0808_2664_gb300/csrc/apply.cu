@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
   }
   const int PG = NT / kw;  // threads per column: one column per lane, PG rows apart
   const int cc = tid % kw, pg = tid / kw;
+  const int nb4 = (n + 3) / 4;  // FP32 phases: blocks of four rows
   if (mode != kApplyForm) {
     // W += Y_b^T C_b; Y_b is upper triangular, so W(p) sums rows i <= p.
     for (int b = 1; b < nc; ++b) {
@@ -390,7 +391,28 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
       }
       load_y(b);
       __syncthreads();
-      if (cc < kc) {
+      if constexpr (sizeof(T) == 4) {
+        // FP32: items (column, four consecutive p), column fastest, so a
+        // warp's Y loads are broadcasts; each C_b entry feeds four products.
+        // Y_b(i, p) = 0 is stored for i > p, so running i to the block's
+        // last p adds only exact zeros after each sum's own terms.
+        for (int item = tid; item < kc * nb4; item += NT) {
+          const int c = item % kc, p0 = 4 * (item / kc);
+          T acc[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[j] = p0 + j < n ? B2[c * ldn + p0 + j] : T(0);
+          const int iend = p0 + 4 < n ? p0 + 4 : n;
+          for (int i = 0; i < iend; ++i) {
+            const T x = B1[c * ldn + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (p0 + j < n) acc[j] = fma(Ys[(p0 + j) * ldn + i], x, acc[j]);
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (p0 + j < n) B2[c * ldn + p0 + j] = acc[j];
+        }
+      } else if (cc < kc) {
         for (int p = pg; p < n; p += PG) {
           T s = B2[cc * ldn + p];
           for (int i = 0; i <= p; ++i) s = fma(Ys[p * ldn + i], B1[cc * ldn + i], s);
@@ -403,7 +425,34 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
   for (int idx = tid; idx < n * n; idx += NT) Ts[idx] = Tg[idx];
   __syncthreads();
   // W' = T^T W (Q^T) or T W (Q, form), into B1.
-  if (cc < kc) {
+  if constexpr (sizeof(T) == 4) {
+    // FP32: items (column, four consecutive p) as above; T's zeros below the
+    // diagonal are stored, so the extra terms are exact zeros (leading for
+    // T W, trailing for T^T W).
+    for (int item = tid; item < kc * nb4; item += NT) {
+      const int c = item % kc, p0 = 4 * (item / kc);
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      if (trans) {
+        const int qend = p0 + 4 < n ? p0 + 4 : n;
+        for (int qq = 0; qq < qend; ++qq) {
+          const T x = B2[c * ldn + qq];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (p0 + j < n) acc[j] = fma(Ts[qq + (p0 + j) * n], x, acc[j]);
+        }
+      } else {
+        for (int qq = p0; qq < n; ++qq) {
+          const T x = B2[c * ldn + qq];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (p0 + j < n) acc[j] = fma(Ts[(p0 + j) + qq * n], x, acc[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (p0 + j < n) B1[c * ldn + p0 + j] = acc[j];
+    }
+  } else if (cc < kc) {
     for (int p = pg; p < n; p += PG) {
       T s = T(0);
       if (trans) {
@@ -427,7 +476,23 @@ __global__ void __launch_bounds__(NT) node_apply_kernel(NodeApplyArgs<T> a) {
     __syncthreads();
     load_y(b);
     __syncthreads();
-    if (cc < kc) {
+    if constexpr (sizeof(T) == 4) {
+      // FP32: items (column, four consecutive rows i); Y_b(i, p) = 0 for
+      // p < i is stored, so the leading extra terms are exact zeros.
+      for (int item = tid; item < kc * nb4; item += NT) {
+        const int c = item % kc, i0 = 4 * (item / kc);
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        for (int p = i0; p < n; ++p) {
+          const T x = B1[c * ldn + p];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (i0 + j < n) acc[j] = fma(Ys[p * ldn + i0 + j], x, acc[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (i0 + j < n) B2[c * ldn + i0 + j] = acc[j];
+      }
+    } else if (cc < kc) {
       for (int i = pg; i < n; i += PG) {
         T s = T(0);
         for (int p = i; p < n; ++p) s = fma(Ys[p * ldn + i], B1[cc * ldn + p], s);
