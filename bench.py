@@ -652,20 +652,6 @@ def ours(args, world, rank, local):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        rate, ms, dt, cores = oracle_rows_per_s(args.m, args.n, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "rows/s", "cores": cores, "kind": "oracle",
-               "sample": f"{ms} x {args.n} rows (factor + thin Q) of the {args.m} x {args.n} workload, {dt:.1f} s"}
-        import oracle as _oracle
-        _oracle.set_num_threads(1)
-        try:
-            r1, ms1, dt1, _ = oracle_rows_per_s(args.m, args.n, args.cpu_seconds)
-        finally:
-            _oracle.set_num_threads(cores)
-        cpu["single_thread"] = {"value": r1, "unit": "rows/s", "cores": 1,
-                                "sample": f"{ms1} x {args.n} rows of the same workload, {dt1:.1f} s"}
-
     tq._lib.lib()
     if dist:
         dist.barrier()
@@ -790,6 +776,22 @@ def ours(args, world, rank, local):
     if "grad" in want:
         variants["grad_fp64_1Mx128"] = grad_run(tq, torch, torch.float64, steps=3, warmup=3)
         variants["grad_fp32_1Mx128"] = grad_run(tq, torch, torch.float32, steps=3, warmup=3)
+
+    # The CPU oracle runs after every GPU measurement, so that its host
+    # threads never share the cores with the timed host-buffer pipeline.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, ms, dt, cores = oracle_rows_per_s(args.m, args.n, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "rows/s", "cores": cores, "kind": "oracle",
+               "sample": f"{ms} x {args.n} rows (factor + thin Q) of the {args.m} x {args.n} workload, {dt:.1f} s"}
+        import oracle as _oracle
+        _oracle.set_num_threads(1)
+        try:
+            r1, ms1, dt1, _ = oracle_rows_per_s(args.m, args.n, args.cpu_seconds)
+        finally:
+            _oracle.set_num_threads(cores)
+        cpu["single_thread"] = {"value": r1, "unit": "rows/s", "cores": 1,
+                                "sample": f"{ms1} x {args.n} rows of the same workload, {dt1:.1f} s"}
 
     if rank == 0:
         line = {
