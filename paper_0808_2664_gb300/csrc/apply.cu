@@ -36,12 +36,20 @@ __device__ __forceinline__ void copy4(int tid, int count, Ld ld, St st) {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 
 // ---------------------------------------------------------------- leaves --
-// Shared memory: Ys [kApplyRows][n+1] (row-major), Cs [kApplyRows][kc+1],
+// Shared memory: Ys [kApplyRows][n+1] (row-major), Cs [kApplyRows][kc+1] (FP32: at
+// least [kApplyRows][n+1], the second Y block of phase 3),
 // Ws [n][kc] (W, then T-times-W), Ts [n][n] (column-major T).
 // Whether a leaf's n x n T fits in the Y and C staging tiles (it is needed
 // only after they are done with).
+// Bytes of the C staging tile [kApplyRows][kApplyCols + 1]; with FP32 it
+// also holds the second 32-row block of Y ([kApplyRows][n + 1]) in phase 3.
+__host__ __device__ inline size_t leaf_apply_cs_bytes(int n, size_t elem) {
+  const int cols = (elem == 4 && n + 1 > kApplyCols + 1) ? n + 1 : kApplyCols + 1;
+  return align16(elem * kApplyRows * (size_t)cols);
+}
+
 __host__ __device__ inline bool leaf_apply_t_shared(int n, size_t elem) {
-  return elem * (size_t)n * n <= align16(elem * kApplyRows * (n + 1)) + align16(elem * kApplyRows * (kApplyCols + 1));
+  return elem * (size_t)n * n <= align16(elem * kApplyRows * (n + 1)) + leaf_apply_cs_bytes(n, elem);
 }
 
 template <typename T, int NT>
@@ -53,7 +61,7 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
   const int ly = n + 1, lc = KC + 1;
   T* Ys = reinterpret_cast<T*>(smem);
   T* Cs = reinterpret_cast<T*>(smem + align16(sizeof(T) * RB * ly));
-  T* Ws = reinterpret_cast<T*>(smem + align16(sizeof(T) * RB * ly) + align16(sizeof(T) * RB * lc));
+  T* Ws = reinterpret_cast<T*>(smem + align16(sizeof(T) * RB * ly) + leaf_apply_cs_bytes(n, sizeof(T)));
   // T is needed only between phases 1 and 3: it reuses the staging area when it fits.
   const bool t_shared = leaf_apply_t_shared(n, sizeof(T));
   T* Ts = t_shared ? Ys : Ws + (size_t)n * KC;
@@ -246,47 +254,75 @@ __global__ void __launch_bounds__(NT) leaf_apply_kernel(LeafApplyArgs<T> a) {
 
   // Phase 3: C <- C - Y W  (form: C <- [X; 0] - Y W).
   if constexpr (sizeof(T) == 4) {
-    // FP32: lane = row of the 32-row block, warp = 8 contiguous columns, all
-    // eight dot products at once (W read as two float4 per p, eight
-    // independent chains, the eight C entries read before any store); each
-    // dot runs over p in order as below, so the results are the same.
+    // FP32: 64-row steps, a lane = rows r and r + 32, a warp = 8 contiguous
+    // columns, all sixteen dot products at once (W read as two float4 per
+    // p, each feeding both rows; the C entries read before any store).  The
+    // first 32 rows come through the prefetch registers, the second 32 are
+    // staged directly into the C tile (unused here).  Y's zeros above the
+    // diagonal and past the leaf are staged, so running both rows' dots to
+    // the longer bound adds only exact zeros after each dot's own terms,
+    // which are taken in order p = 0, 1, ...
     static_assert(RB == 32 && (NT / 32) * 8 == KC, "phase 3 layout: a warp per 8 columns of a 32-row block");
+    T* Ys2 = Cs;
     const int i = tid & 31, c0 = (tid >> 5) * 8;
-    if (kPrefetch) fetch_y(0, hl);
-    for (int rb = 0; rb < hl; rb += RB) {
+    fetch_y(0, hl);
+    for (int rb = 0; rb < hl; rb += 2 * RB) {
       __syncthreads();
-      if (kPrefetch) stage_y();
-      else direct_y(rb, hl);
+      stage_y();
+      copy4<NT>(
+          tid, RB * n,
+          [&](int idx) {
+            const int ii = idx % RB, p = idx / RB, r = rb + RB + ii;
+            T v = T(0);
+            if (r < hl) v = r < p ? T(0) : (r == p ? T(1) : Yg[r + (int64_t)p * a.ldy]);
+            return v;
+          },
+          [&](int idx, T v) { Ys2[(idx % RB) * ly + idx / RB] = v; });
       __syncthreads();
-      if (kPrefetch && rb + RB < hl) fetch_y(rb + RB, hl);
-      const int r = rb + i;
-      if (r < hl && c0 < kc) {
-        const int pmax = min(n, r + 1);  // Y(r, p) = 0 for p > r
-        const bool fresh = mode == kApplyForm && r >= n;  // rows below X start from zero
-        T* row = Cg + r;
-        T old[8], acc[8];
+      if (rb + 2 * RB < hl) fetch_y(rb + 2 * RB, hl);
+      const int ra = rb + i, rbb = rb + RB + i;
+      if (ra < hl && c0 < kc) {
+        const bool two = rbb < hl;
+        const int pmax = min(n, (two ? rbb : ra) + 1);  // Y(r, p) = 0 for p > r
+        T acc[2][8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          old[j] = (c0 + j < kc && !fresh) ? row[(int64_t)(c0 + j) * a.ldc] : T(0);
-          acc[j] = T(0);
-        }
-        const T* yr = Ys + i * ly;
+        for (int j = 0; j < 8; ++j) acc[0][j] = acc[1][j] = T(0);
+        const T* ya = Ys + i * ly;
+        const T* yb = Ys2 + i * ly;
         for (int p = 0; p < pmax; ++p) {
-          const T y = yr[p];
+          const T y0 = ya[p], y1 = yb[p];
           const float4 w0 = *reinterpret_cast<const float4*>(Ws + p * KC + c0);
           const float4 w1 = *reinterpret_cast<const float4*>(Ws + p * KC + c0 + 4);
-          acc[0] = fma(y, w0.x, acc[0]);
-          acc[1] = fma(y, w0.y, acc[1]);
-          acc[2] = fma(y, w0.z, acc[2]);
-          acc[3] = fma(y, w0.w, acc[3]);
-          acc[4] = fma(y, w1.x, acc[4]);
-          acc[5] = fma(y, w1.y, acc[5]);
-          acc[6] = fma(y, w1.z, acc[6]);
-          acc[7] = fma(y, w1.w, acc[7]);
+          acc[0][0] = fma(y0, w0.x, acc[0][0]);
+          acc[0][1] = fma(y0, w0.y, acc[0][1]);
+          acc[0][2] = fma(y0, w0.z, acc[0][2]);
+          acc[0][3] = fma(y0, w0.w, acc[0][3]);
+          acc[0][4] = fma(y0, w1.x, acc[0][4]);
+          acc[0][5] = fma(y0, w1.y, acc[0][5]);
+          acc[0][6] = fma(y0, w1.z, acc[0][6]);
+          acc[0][7] = fma(y0, w1.w, acc[0][7]);
+          acc[1][0] = fma(y1, w0.x, acc[1][0]);
+          acc[1][1] = fma(y1, w0.y, acc[1][1]);
+          acc[1][2] = fma(y1, w0.z, acc[1][2]);
+          acc[1][3] = fma(y1, w0.w, acc[1][3]);
+          acc[1][4] = fma(y1, w1.x, acc[1][4]);
+          acc[1][5] = fma(y1, w1.y, acc[1][5]);
+          acc[1][6] = fma(y1, w1.z, acc[1][6]);
+          acc[1][7] = fma(y1, w1.w, acc[1][7]);
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (c0 + j < kc) row[(int64_t)(c0 + j) * a.ldc] = old[j] - acc[j];
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int r = h2 ? rbb : ra;
+          if (h2 && !two) break;
+          const bool fresh = mode == kApplyForm && r >= n;  // rows below X start from zero
+          T* row = Cg + r;
+          T old[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) old[j] = (c0 + j < kc && !fresh) ? row[(int64_t)(c0 + j) * a.ldc] : T(0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (c0 + j < kc) row[(int64_t)(c0 + j) * a.ldc] = old[j] - acc[h2][j];
+        }
       }
     }
     return;
@@ -570,7 +606,7 @@ inline unsigned small_grid(int64_t work) {
 }  // namespace
 
 size_t leaf_apply_smem(int n, size_t elem) {
-  return align16(elem * kApplyRows * (n + 1)) + align16(elem * kApplyRows * (kApplyCols + 1)) +
+  return align16(elem * kApplyRows * (n + 1)) + leaf_apply_cs_bytes(n, elem) +
          elem * (size_t)n * kApplyCols + (leaf_apply_t_shared(n, elem) ? 0 : elem * (size_t)n * n);
 }
 
