@@ -14,7 +14,9 @@ Prints one JSON line (rank 0).  Also reports:
   cpu_baseline  the CPU oracle (plain Householder QR + form Q) on a bounded
                 row sample, on this host's cores;
   e2e           the same step through the public API with host buffers:
-                pinned H2D copy of A, factor, form Q, D2H copy of Q and R;
+                pinned H2D copy of A, factor, form Q, D2H copy of Q and R
+                (with each timed step's span, and the pinned copy rates
+                measured alone);
   variants      the mixed-precision form (FP32 storage, FP64 reflectors) on
                 the same shape.
 `--impl reference` times the CPU oracle alone (the reference arm).
@@ -512,13 +514,16 @@ def e2e_run(tq, torch, args, q, steps, warmup):
     for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
+    # One event between consecutive steps on the same stream: the total is the first to the
+    # last, and the per-step spans show whether the copies stalled in some steps.
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    evs[0].record(stream)
+    for i in range(steps):
         step()
-    e1.record(stream)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [round(evs[i].elapsed_time(evs[i + 1]), 3) for i in range(steps)]
     es = 8
     # Plain pinned copies of the same buffers, each alone: the end-to-end step cannot beat
     # max(H2D, device work) + max(D2H, form) when the copies overlap only their own phase.
@@ -536,7 +541,7 @@ def e2e_run(tq, torch, args, q, steps, warmup):
     h2d = copy_gbs(lambda: A.copy_(Ah, non_blocking=True))
     d2h = copy_gbs(lambda: Qh.copy_(Q, non_blocking=True))
     return {"value": m * steps / (ms / 1e3), "unit": "rows/s", "h2d_bytes_per_step": m * n * es,
-            "d2h_bytes_per_step": m * n * es + n * n * es, "ms_per_step": ms / steps,
+            "d2h_bytes_per_step": m * n * es + n * n * es, "ms_per_step": ms / steps, "step_ms": step_ms,
             "pinned_h2d_gbs": h2d, "pinned_d2h_gbs": d2h, "host_cpus": sorted(os.sched_getaffinity(0))[:1] +
             sorted(os.sched_getaffinity(0))[-1:], "gpu_numa_node": _gpu_numa_node(torch)}
 
