@@ -132,10 +132,15 @@ def reference_arm(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+L2_BYTES = 129 * 2**20  # GB300 L2
+
+
 def workload_config(args, dtype="f64"):
+    nbytes = args.m * args.n * (8 if dtype == "f64" else 4)
+    l2 = (f"inputs ({nbytes / 1e9:.1f} GB) larger than L2; no flush" if nbytes > L2_BYTES else
+          f"inputs ({nbytes / 1e6:.1f} MB) fit in L2; no flush (warm-L2 figures)")
     return {"workload": f"tsqr_factor+form_q {dtype} m={args.m} n={args.n} gaussian",
-            "m": args.m, "n": args.n, "leaf_rows": args.leaf_rows, "arity": args.arity,
-            "l2": "inputs (2.1 GB) larger than L2; no flush"}
+            "m": args.m, "n": args.n, "leaf_rows": args.leaf_rows, "arity": args.arity, "l2": l2}
 
 
 # ------------------------------------------------------------------ clocks --
