@@ -14,9 +14,10 @@ Prints one JSON line (rank 0).  Also reports:
   cpu_baseline  the CPU oracle (plain Householder QR + form Q) on a bounded
                 row sample, on this host's cores;
   e2e           the same step through the public API with host buffers:
-                pinned H2D copy of A, factor, form Q, D2H copy of Q and R
-                (with each timed step's span, and the pinned copy rates
-                measured alone);
+                A read from pinned host memory by the leaf kernel, factor,
+                form Q stored into pinned host memory, R back to the host
+                (with each timed step's span, and the copy engines' pinned
+                rates measured alone);
   variants      the mixed-precision form (FP32 storage, FP64 reflectors) on
                 the same shape.
 `--impl reference` times the CPU oracle alone (the reference arm).
@@ -496,8 +497,9 @@ def measured_hbm():
 
 
 def e2e_run(tq, torch, args, q, steps, warmup):
-    """Public API with host buffers (tsqr_factor_form_host): H2D of A, factor, form Q, D2H of Q and R
-    each step, inside the timed region."""
+    """Public API with host buffers (tsqr_factor_form_host), each step inside the timed region: A
+    read from pinned host memory by the leaf kernel, factor, form Q into pinned host memory, R to
+    the host."""
     m, n = args.m, args.n
     dtype = torch.float64
     from paper_0808_2664_gb300 import inputs
@@ -513,8 +515,9 @@ def e2e_run(tq, torch, args, q, steps, warmup):
     stream = torch.cuda.current_stream()
 
     def step():
-        # One library call: pinned host A in, host Q and R out, copies pipelined with the leaves.
-        q.factor_form_host(Ah, Qh, Rh, A, Q, R)
+        # One library call: pinned host A in (read by the leaf kernel over the host link), host Q
+        # and R out (Q stored by the form kernels straight into the pinned Q_host).
+        q.factor_form_host(Ah, Qh, Rh, A, None, R)
 
     for _ in range(warmup):
         step()

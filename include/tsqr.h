@@ -173,21 +173,29 @@ int tsqr_form_q_mul(tsqr_q_t q, int64_t k, const void* X, int64_t ldx, void* Q, 
  * tsqr_factor_form_host: A = QR of a HOST matrix, with thin Q and R written
  * back to HOST memory (Section 2.1: factor, then the Q factor with n
  * columns), for data that lives on the host.  One call = tsqr_refactor +
- * tsqr_form_q + the copies, pipelined: A goes to the device in chunks of
- * leaves on a copy stream owned by the handle while the leaves already
- * there are factored on `stream`; after the tree and the tree part of Q,
- * Q comes back chunk by chunk as its leaves are formed.
- *   A_host (m x n, column-major, lda_host >= m), read; Q_host (m x n,
+ * tsqr_form_q + the host transfers:
+ *   - a page-locked A_host (cudaHostAlloc or cudaHostRegister) is read by
+ *     the leaf kernel itself over the host link, leaf by leaf; a pageable
+ *     one goes to the device in chunks of leaves on a copy stream owned by
+ *     the handle while the leaves already there are factored on `stream`;
+ *   - after the tree and the tree part of Q: with a device Q, Q comes back
+ *     chunk by chunk (copy stream) as its leaves are formed; with Q = NULL
+ *     the form kernels store Q straight into Q_host, which must then be
+ *     page-locked;
+ *   - R goes to R_host after the tree (by a kernel when R_host is
+ *     page-locked, else by a copy).
+ *   A_host (m x n, column-major, lda_host >= m), read only; Q_host (m x n,
  *   ldq_host >= m) and R_host (n x n upper triangular, diag >= 0,
- *   ldr_host >= n), written.  Page-locked host memory lets the copies
- *   overlap the kernels; pageable memory works, without the overlap.
- *   A, Q, R: device buffers of the same shapes (lda, ldq >= m, ldr >= n),
+ *   ldr_host >= n), written.
+ *   A, R: device buffers of the same shapes (lda >= m, ldr >= n),
  *   caller-owned; A ends holding the Householder vectors (the handle
- *   borrows it, as after tsqr_refactor), Q the thin Q, R the R factor.
- *   Q must not alias A.
+ *   borrows it, as after tsqr_refactor), R the R factor.  Q: a device
+ *   buffer (ldq >= m) that ends holding the thin Q, or NULL; not A.
  * Asynchronous on `stream`: when `stream` reaches the end of the call, all
- * host outputs are written.  Returns TSQR_OK, TSQR_ERR_HANDLE, -i for
- * argument i (2..13) invalid, or a CUDA error code.
+ * host outputs are written.  Returns TSQR_OK, TSQR_ERR_HANDLE,
+ * TSQR_ERR_UNSUPPORTED (hybrid or flat trees), -i for argument i (2..13)
+ * invalid (-10 also for Q = NULL with a pageable Q_host), or a CUDA error
+ * code.
  */
 int tsqr_factor_form_host(tsqr_q_t q, const void* A_host, int64_t lda_host, void* Q_host, int64_t ldq_host,
                           void* R_host, int64_t ldr_host, void* A, int64_t lda, void* Q, int64_t ldq, void* R,

@@ -165,17 +165,19 @@ class QTree:
         return Q
 
     def factor_form_host(self, A_host, Q_host, R_host, A, Q, R):
-        """QR of a host matrix with Q and R written back to host memory, the copies pipelined
-        with the leaf work (tsqr_factor_form_host).  A_host, Q_host, R_host: column-major CPU
-        tensors (pinned for overlap); A, Q, R: device tensors of the same shapes.  Asynchronous
-        on the current stream of A's device."""
+        """QR of a host matrix with Q and R written back to host memory (tsqr_factor_form_host).
+        A_host, Q_host, R_host: column-major CPU tensors; pinned ones are read and written by
+        the kernels themselves, pageable ones go through copies.  A, R: device tensors of the
+        same shapes; Q: a device tensor, or None to have Q stored straight into a pinned
+        Q_host.  Asynchronous on the current stream of A's device."""
         if tuple(A_host.shape) != (self.m, self.n) or A_host.dtype != self.dtype:
             raise ValueError("A_host does not match the handle's shape / dtype")
         check(lib().tsqr_factor_form_host(
             self.ptr, ctypes.c_void_p(A_host.data_ptr()), _ld(A_host, "A_host", host=True),
             ctypes.c_void_p(Q_host.data_ptr()), _ld(Q_host, "Q_host", host=True),
             ctypes.c_void_p(R_host.data_ptr()), _ld(R_host, "R_host", host=True),
-            ctypes.c_void_p(A.data_ptr()), _ld(A, "A"), ctypes.c_void_p(Q.data_ptr()), _ld(Q, "Q"),
+            ctypes.c_void_p(A.data_ptr()), _ld(A, "A"),
+            ctypes.c_void_p(Q.data_ptr() if Q is not None else None), _ld(Q, "Q") if Q is not None else 0,
             ctypes.c_void_p(R.data_ptr()), _ld(R, "R"), _stream(A)), "tsqr_factor_form_host")
         self.A = A
         return Q_host, R_host

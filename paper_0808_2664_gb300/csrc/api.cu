@@ -317,11 +317,14 @@ int64_t leaf_row0(const tsqr_q_s* q, int64_t l) { return l >= q->nleaves ? q->m 
 
 // Leaf QR of leaves [l0, l1) (the same kernel on a sub-range).
 template <typename T>
-cudaError_t launch_leaf_range(tsqr_q_s* q, T* A, int64_t lda, int64_t l0, int64_t l1, cudaStream_t s) {
+cudaError_t launch_leaf_range(tsqr_q_s* q, T* A, int64_t lda, int64_t l0, int64_t l1, cudaStream_t s,
+                              const T* Asrc = nullptr, int64_t ldsrc = 0) {
   const int64_t nn = q->n * q->n, r0 = leaf_row0(q, l0);
   LeafFactorArgs<T> la{};
   la.A = A + r0;
   la.lda = lda;
+  la.Asrc = Asrc ? Asrc + r0 : nullptr;  // the recursive leaf reads A only (callers do not pass a source)
+  la.ldsrc = ldsrc;
   la.m = leaf_row0(q, l1) - r0;
   la.n = (int)q->n;
   la.h = q->h;
@@ -536,46 +539,87 @@ cudaError_t run_tree_form(const tsqr_q_s* q, T* C, int64_t ldc, cudaStream_t s, 
   return e;
 }
 
-// Host-buffer pipeline: A arrives in chunks of leaves on the copy stream
-// while the compute stream factors the chunks already in; the tree and the
-// tree part of forming Q follow; then Q leaves the device chunk by chunk
-// as the form finishes each one.  Chunks are whole waves of leaf CTAs.
+// Copies a rows x cols column-major block (the n x n R into a mapped host
+// buffer, so that the call queues no copy-engine transfer).
+template <typename T>
+__global__ void copy_block_kernel(const T* __restrict__ src, int64_t lds, T* __restrict__ dst, int64_t ldd,
+                                  int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, i = e - c * rows;
+    dst[c * ldd + i] = src[c * lds + i];
+  }
+}
+
+// Address at which kernels can reach a page-locked host buffer (allocated
+// with cudaHostAlloc or registered); null for pageable memory.
+template <typename T>
+T* mapped_host(const T* p) {
+  cudaPointerAttributes at{};
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost && at.devicePointer ? (T*)at.devicePointer : nullptr;
+}
+
+// Host-buffer pipeline.  A page-locked A_host is read by the leaf kernel
+// itself, over the host link, as it loads each leaf (Y and R_i go to the
+// device A); a pageable one arrives in chunks of leaves on the copy stream
+// while the compute stream factors the chunks already in.  The tree and the
+// tree part of forming Q follow.  With a device Q, Q leaves the device chunk
+// by chunk as the form finishes each one; with none, the form kernels store
+// Q straight into the page-locked Q_host.  Chunks are whole waves of leaf
+// CTAs.  Copy-engine transfers of page-locked memory were measured to stall
+// for tens of milliseconds now and then where the SMs' own loads and stores
+// to the same buffers did not.
 template <typename T>
 cudaError_t run_factor_form_host(tsqr_q_s* q, const T* Ah, int64_t ldah, T* Qh, int64_t ldqh, T* Rh, int64_t ldrh,
                                  T* A, int64_t lda, T* Q, int64_t ldq, T* R, int64_t ldr, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
+  const T* dAh = q->rec ? nullptr : mapped_host(Ah);
+  T* dQh = Q ? nullptr : mapped_host(Qh);
+  if (!Q && !dQh) return cudaErrorInvalidValue;
+  T* dRh = mapped_host(Rh);
   int dev = 0, sms = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   int64_t chunk = 4 * (int64_t)sms;  // four waves of one-CTA-per-SM leaves
   if (chunk > q->nleaves) chunk = q->nleaves;
   const int64_t nchunks = (q->nleaves + chunk - 1) / chunk;
-  if (!q->copy && (e = cudaStreamCreateWithFlags(&q->copy, cudaStreamNonBlocking)) != cudaSuccess) return e;
-  if (!q->ev_start && (e = cudaEventCreateWithFlags(&q->ev_start, cudaEventDisableTiming)) != cudaSuccess) return e;
-  if (!q->ev_done && (e = cudaEventCreateWithFlags(&q->ev_done, cudaEventDisableTiming)) != cudaSuccess) return e;
-  while ((int64_t)q->ev_in.size() < nchunks) {
-    cudaEvent_t a = nullptr, b = nullptr;
-    if ((e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming)) != cudaSuccess) return e;
-    if ((e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming)) != cudaSuccess) {
-      cudaEventDestroy(a);
-      return e;
-    }
-    q->ev_in.push_back(a);
-    q->ev_out.push_back(b);
-  }
   const size_t es = sizeof(T);
-  // The copy stream starts after everything already queued on s.
-  if ((e = cudaEventRecord(q->ev_start, s)) != cudaSuccess) return e;
-  if ((e = cudaStreamWaitEvent(q->copy, q->ev_start, 0)) != cudaSuccess) return e;
-  for (int64_t c = 0; c < nchunks; ++c) {
-    const int64_t l0 = c * chunk, l1 = l0 + chunk < q->nleaves ? l0 + chunk : q->nleaves;
-    const int64_t r0 = leaf_row0(q, l0), r1 = leaf_row0(q, l1);
-    if ((e = cudaMemcpy2DAsync(A + r0, lda * es, Ah + r0, ldah * es, (r1 - r0) * es, q->n, cudaMemcpyHostToDevice,
-                               q->copy)) != cudaSuccess)
-      return e;
-    if ((e = cudaEventRecord(q->ev_in[c], q->copy)) != cudaSuccess) return e;
+  const bool copies = !dAh || Q;  // anything on the copy stream
+  if (copies) {
+    if (!q->copy && (e = cudaStreamCreateWithFlags(&q->copy, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if (!q->ev_start && (e = cudaEventCreateWithFlags(&q->ev_start, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if (!q->ev_done && (e = cudaEventCreateWithFlags(&q->ev_done, cudaEventDisableTiming)) != cudaSuccess) return e;
+    while ((int64_t)q->ev_in.size() < nchunks) {
+      cudaEvent_t a = nullptr, b = nullptr;
+      if ((e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming)) != cudaSuccess) return e;
+      if ((e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming)) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+      }
+      q->ev_in.push_back(a);
+      q->ev_out.push_back(b);
+    }
+    // The copy stream starts after everything already queued on s.
+    if ((e = cudaEventRecord(q->ev_start, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(q->copy, q->ev_start, 0)) != cudaSuccess) return e;
   }
-  {
+  if (dAh) {
+    StageTimer t0(q, TSQR_STAGE_LEAF_FACTOR, s);
+    if ((e = launch_leaf_range(q, A, lda, 0, q->nleaves, s, dAh, ldah)) != cudaSuccess) return e;
+    t0.stop(1);
+  } else {
+    for (int64_t c = 0; c < nchunks; ++c) {
+      const int64_t l0 = c * chunk, l1 = l0 + chunk < q->nleaves ? l0 + chunk : q->nleaves;
+      const int64_t r0 = leaf_row0(q, l0), r1 = leaf_row0(q, l1);
+      if ((e = cudaMemcpy2DAsync(A + r0, lda * es, Ah + r0, ldah * es, (r1 - r0) * es, q->n, cudaMemcpyHostToDevice,
+                                 q->copy)) != cudaSuccess)
+        return e;
+      if ((e = cudaEventRecord(q->ev_in[c], q->copy)) != cudaSuccess) return e;
+    }
     StageTimer t0(q, TSQR_STAGE_LEAF_FACTOR, s);
     for (int64_t c = 0; c < nchunks; ++c) {
       const int64_t l0 = c * chunk, l1 = l0 + chunk < q->nleaves ? l0 + chunk : q->nleaves;
@@ -588,10 +632,20 @@ cudaError_t run_factor_form_host(tsqr_q_s* q, const T* Ah, int64_t ldah, T* Qh, 
   q->A = A;
   q->lda = lda;
   q->factored = true;
-  if ((e = cudaMemcpy2DAsync(Rh, ldrh * es, R, ldr * es, q->n * es, q->n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  if (dRh) {
+    const int64_t nn = q->n * q->n;
+    copy_block_kernel<T><<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(R, ldr, dRh, ldrh, q->n, q->n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if ((e = cudaMemcpy2DAsync(Rh, ldrh * es, R, ldr * es, q->n * es, q->n, cudaMemcpyDeviceToHost, s)) !=
+             cudaSuccess) {
     return e;
-  if ((e = run_tree_form(q, Q, ldq, s)) != cudaSuccess) return e;
-  {
+  }
+  if (!Q) {
+    // Q straight into Q_host: the same form as tsqr_form_q.
+    if ((e = run_apply<T>(q, kApplyForm, q->n, dQh, ldqh, s)) != cudaSuccess) return e;
+    if (!copies) return cudaSuccess;
+  } else {
+    if ((e = run_tree_form(q, Q, ldq, s)) != cudaSuccess) return e;
     StageTimer t(q, TSQR_STAGE_LEAF_APPLY, s);
     for (int64_t c = 0; c < nchunks; ++c) {
       const int64_t l0 = c * chunk, l1 = l0 + chunk < q->nleaves ? l0 + chunk : q->nleaves;
@@ -803,8 +857,8 @@ int tsqr_factor_form_host(tsqr_q_t q, const void* A_host, int64_t lda_host, void
   if (ldr_host < n) return -7;
   if (!A) return -8;
   if (lda < m) return -9;
-  if (!Q || Q == A) return -10;
-  if (ldq < m) return -11;
+  if (Q == A || (!Q && !mapped_host(static_cast<const char*>(Q_host)))) return -10;
+  if (Q && ldq < m) return -11;
   if (!R) return -12;
   if (ldr < n) return -13;
   cudaStream_t s = (cudaStream_t)stream;

@@ -111,9 +111,14 @@ __device__ __forceinline__ int leaf_groups(int threads, int rows) {
 // Householder vectors are e_k on top and a dense column below; the dense
 // part is written to all hl - n rows of Ag and the new R to Rl (which may be
 // Rtop: Rtop is read before Rl is written).
+//
+// As (column stride ldas), when given, is where the leaf's rows are read
+// from; Y and R_i are still written to Ag.  A mapped page-locked host
+// matrix there lets the leaf load its tile over the host link itself.
 template <typename T, int NT, int NMAX, bool kWantT = true, bool kStacked = false>
 __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl, T* taul, T* Tg, int* status,
-                                unsigned char* smem, const T* Rtop = nullptr) {
+                                unsigned char* smem, const T* Rtop = nullptr, const T* As = nullptr,
+                                int64_t ldas = 0) {
   static_assert(NT >= 128, "the leaf schedule needs at least four warps");
   T* S = reinterpret_cast<T*>(smem);
   unsigned char* aux = smem + leaf_tile_region(n, ld, sizeof(T));
@@ -159,9 +164,11 @@ __device__ void leaf_factor_one(T* Ag, int64_t lda, int hl, int n, int ld, T* Rl
   // Load the tile: each thread walks the column-major elements e = tid + t NT,
   // several loads in flight.
   const int top = kStacked ? n : 0;  // rows of the tile taken from Rtop
+  const T* const Ls = As ? As : Ag;
+  const int64_t lls = As ? ldas : lda;
   auto src = [&](int c, int i) -> T {
-    if constexpr (kStacked) return i < n ? Rtop[c * n + i] : Ag[(int64_t)c * lda + (i - n)];
-    else return Ag[(int64_t)c * lda + i];
+    if constexpr (kStacked) return i < n ? Rtop[c * n + i] : Ls[(int64_t)c * lls + (i - n)];
+    else return Ls[(int64_t)c * lls + i];
   };
   {
     const int total = hl * n;

@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 1024 / NT : 1) leaf_facto
     const int64_t r0 = leaf * a.h;
     const int hl = (leaf == a.nleaves - 1) ? (int)(a.m - r0) : (int)a.h;
     leaf_factor_one<T, NT, NMAX>(a.A + r0, a.lda, hl, a.n, a.ld_s, a.R + leaf * nn, a.tau + leaf * (int64_t)a.n,
-                                 a.Tw + leaf * nn, a.status, smem);
+                                 a.Tw + leaf * nn, a.status, smem, nullptr, a.Asrc ? a.Asrc + r0 : nullptr,
+                                 a.ldsrc);
   }
 }
 

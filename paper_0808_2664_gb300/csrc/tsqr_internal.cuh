@@ -47,6 +47,10 @@ struct LeafFactorArgs {
   T* tau;           // nleaves x n
   T* Tw;            // nleaves x (n x n): compact-WY T of each leaf
   int* status;
+  // When set, the leaf rows are read from here (column stride ldsrc; for
+  // example a mapped page-locked host matrix) and only written to A.
+  const T* Asrc;
+  int64_t ldsrc;
 };
 
 // Structured QR of up to q stacked triangles per node (Section 2.1,

@@ -240,29 +240,72 @@ def test_plan_once_refactor_matches():
         assert np.linalg.norm(A - Q @ host(R)) / np.linalg.norm(A) <= fp64_tol(m, n)
 
 
+@pytest.mark.parametrize("mode", ["pinned", "pinned_no_device_q", "pageable"])
 @pytest.mark.parametrize("m,n,h", [(100_000, 8, 32), (50_000, 16, 64), (3000, 32, 256)])
-def test_factor_form_host_pipeline(oracle_mod, m, n, h):
-    """Host-buffer call (chunked copies overlapped with the leaves) equals the device calls bitwise
-    and the oracle within the bound; several chunks of leaves and a merged last leaf."""
+def test_factor_form_host_pipeline(oracle_mod, m, n, h, mode):
+    """Host-buffer call equals the device calls bitwise and the oracle within the bound; several
+    chunks of leaves and a merged last leaf.  Pinned A_host: the leaf kernel loads it itself;
+    with no device Q the form stores Q straight into the pinned Q_host; pageable buffers go
+    through chunked copies."""
     A = inputs.gaussian(m, n, 21)
     q = tq.tsqr_q_create(m, n, torch.float64, "cuda", leaf_rows=h)
-    Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
+    pin = mode != "pageable"
+    Ah = torch.empty((n, m), dtype=torch.float64, pin_memory=pin).t()
     Ah.copy_(torch.from_numpy(A))
-    Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=True).t()
-    Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    Qh = torch.empty((n, m), dtype=torch.float64, pin_memory=pin).t()
+    Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=pin).t()
     Ad, Qd, Rd = tq.colmajor(m, n, torch.float64), tq.colmajor(m, n, torch.float64), tq.colmajor(n, n, torch.float64)
-    q.factor_form_host(Ah, Qh, Rh, Ad, Qd, Rd)
+    q.factor_form_host(Ah, Qh, Rh, Ad, None if mode == "pinned_no_device_q" else Qd, Rd)
     torch.cuda.synchronize()
     assert q.sync_status() == 0
+    assert torch.equal(Ah, torch.from_numpy(A))  # A_host is only read
     R1, q1 = tq.tsqr_factor(dev(A), leaf_rows=h, arity=q.info()["arity"])
     Q1 = q1.form_q()
-    assert torch.equal(Rh, R1.cpu()) and torch.equal(Qh, Q1.cpu())
+    assert torch.equal(Rh, R1.cpu()) and torch.equal(Qh, Q1.cpu()) and torch.equal(Rd, R1)
+    if mode != "pinned_no_device_q":
+        assert torch.equal(Qd, Q1)
     Qo, Ro = oracle_mod.qr(A)
     tol = fp64_tol(m, n) * np.linalg.cond(A)
     assert np.linalg.norm(Rh.numpy() - Ro) / np.linalg.norm(Ro) <= tol
     assert np.linalg.norm(Qh.numpy() - Qo) <= tol * n ** 0.5
+    # The handle keeps the factors: Q^T of a device copy of A gives [R; 0] in its top rows.
+    C = dev(A)
+    q.apply_qt(C)
+    assert torch.equal(C[:n], q1.apply_qt(dev(A))[:n])
     q.destroy()
     q1.destroy()
+
+
+def test_factor_form_host_fp32_direct():
+    """FP32 storage through the host call with pinned buffers and no device Q equals the device
+    calls bitwise."""
+    m, n, h = 40_000, 32, 256
+    A = inputs.gaussian(m, n, 22).astype(np.float32)
+    q = tq.tsqr_q_create(m, n, torch.float32, "cuda", leaf_rows=h)
+    Ah = torch.empty((n, m), dtype=torch.float32, pin_memory=True).t()
+    Ah.copy_(torch.from_numpy(A))
+    Qh = torch.empty((n, m), dtype=torch.float32, pin_memory=True).t()
+    Rh = torch.empty((n, n), dtype=torch.float32, pin_memory=True).t()
+    Ad, Rd = tq.colmajor(m, n, torch.float32), tq.colmajor(n, n, torch.float32)
+    q.factor_form_host(Ah, Qh, Rh, Ad, None, Rd)
+    torch.cuda.synchronize()
+    assert q.sync_status() == 0
+    R1, q1 = tq.tsqr_factor(dev(A, torch.float32), leaf_rows=h, arity=q.info()["arity"])
+    Q1 = q1.form_q()
+    assert torch.equal(Rh, R1.cpu()) and torch.equal(Qh, Q1.cpu())
+    q.destroy()
+    q1.destroy()
+
+
+def test_factor_form_host_rejects_pageable_q_without_device_q():
+    m, n = 4096, 8
+    q = tq.tsqr_q_create(m, n, torch.float64, "cuda")
+    Ah = torch.zeros((n, m), dtype=torch.float64, pin_memory=True).t()
+    Qh = torch.empty((n, m), dtype=torch.float64).t()  # pageable
+    Rh = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    with pytest.raises(RuntimeError, match="-10"):
+        q.factor_form_host(Ah, Qh, Rh, tq.colmajor(m, n, torch.float64), None, tq.colmajor(n, n, torch.float64))
+    q.destroy()
 
 
 def test_leaf_compact_wy_t_matches_oracle(oracle_mod):
