@@ -192,7 +192,8 @@ int tsqr_form_q_mul(tsqr_q_t q, int64_t k, const void* X, int64_t ldx, void* Q, 
  *   borrows it, as after tsqr_refactor), R the R factor.  Q: a device
  *   buffer (ldq >= m) that ends holding the thin Q, or NULL; not A.
  * Asynchronous on `stream`: when `stream` reaches the end of the call, all
- * host outputs are written.  Returns TSQR_OK, TSQR_ERR_HANDLE,
+ * host outputs are written; until then A_host must not change (the kernels
+ * or copies may still be reading it).  Returns TSQR_OK, TSQR_ERR_HANDLE,
  * TSQR_ERR_UNSUPPORTED (hybrid or flat trees), -i for argument i (2..13)
  * invalid (-10 also for Q = NULL with a pageable Q_host), or a CUDA error
  * code.
